@@ -1,0 +1,556 @@
+/*
+ * fic_oracle.c -- plain CPU oracle for the modified fast fractal encoder of
+ * Salarian & Miar Naimi, "Modified Fast Fractal Image Compression Algorithm in
+ * spatial domain" (arXiv 1502.00324).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may load this
+ * library: only tests/, __graft_entry__.smoke() and the cpu_baseline /
+ * reference legs of bench.py do.  It shares no code, header, table or helper
+ * with the CUDA path; the two meet only in the seeded input images.
+ *
+ * Every step is written as a plain loop in the paper's order:
+ *   Sec. 2    ranges: non-overlapping BxB blocks, left->right, top->bottom;
+ *             domains: all 2Bx2B blocks at integer step L, decimated 2x2;
+ *             the eight isometries (rotations by 0/90/180/270 degrees
+ *             clockwise, and each one mirrored).
+ *   Eq. 1     E(R,D) = sum_i (S d_i + O - r_i)^2.
+ *   Eq. 3     O = mean(R) - S mean(D)   (least-squares optimal offset).
+ *   Eq. 5-6   block entropy from grey-level counts (here in bits).
+ *   Sec. 3    domain pool = domains with entropy greater than a threshold.
+ *   Sec. 3.2  predefined contrast factors S per step instead of a search.
+ *   Sec. 2    quadtree steps: a range whose error exceeds the step threshold
+ *             splits into four; the last step stores its best mapping anyway.
+ *   Sec. 3.3  stored record: step, range mean, isometry, domain address, S.
+ *   Eq. 4     PSNR.
+ *
+ * Readings of points the paper leaves open (each also listed in the design doc):
+ *   - decimation is the 2x2 average, carried as the integer 2x2 SUM d' so
+ *     that d = d'/4 and all arithmetic stays integral;
+ *   - S = p/q with one common denominator q per step;
+ *   - selection and the split test use the exact error at the optimal
+ *     (unquantised) offset: the integer score 16 q^2 n E(S, O*) with
+ *     n = B*B, written out below;
+ *   - ties go to the lowest (pool index, isometry, S index);
+ *   - the split test is "RMS error > tol" with tol quantised to 1/16 grey
+ *     level (e16 = round(16 tol));
+ *   - the stored offset is the range mean quantised to 7 bits,
+ *     o_q = min(127, floor(sum(r) / (2n))), decoded as 2 o_q + 1;
+ *   - entropy threshold < 0 admits every domain; an empty pool at a
+ *     non-final step splits every range, at the final step it stores a
+ *     mean-only record (pool index 0xFFFFFFFF);
+ *   - decoding starts from a constant 128 image and applies all mappings to
+ *     the previous iterate (Jacobi) until a fixed point or a cap.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------ */
+/* Records and options (layouts private to the oracle).                */
+/* ------------------------------------------------------------------ */
+
+/* One stored record per coded range (Sec. 3.3, Fig. 7).  Positions are kept
+ * explicitly for checking; score is the exact 16 q^2 n E of the mapping. */
+typedef struct {
+    int32_t rx, ry;       /* range top-left, pixels                       */
+    int32_t level;        /* quadtree step, 0 = largest block            */
+    int32_t B;            /* range side                                   */
+    int32_t iso;          /* isometry index 0..7                          */
+    int32_t s_idx;        /* index into the step's S set, -1: mean only   */
+    int32_t o_q;          /* 7-bit range mean                             */
+    int32_t dx, dy;       /* domain top-left, pixels                      */
+    uint32_t pool_idx;    /* address in the step's domain list           */
+    int64_t score;        /* 16 q^2 n E at the optimal offset             */
+} or_code;
+
+#define OR_MAX_S 16
+#define OR_MAX_LEVELS 5
+
+typedef struct {
+    int n_s;              /* number of contrast factors at this step      */
+    int q;                /* common denominator                           */
+    int p[OR_MAX_S];      /* S_i = p[i] / q                               */
+} or_sset;
+
+/* A step's domain pool: the admitted 2Bx2B positions in raster order and
+ * their decimated blocks (B x B sums of 2x2 pixels). */
+typedef struct {
+    int B, L, n_pos;           /* side, step, number of candidate positions */
+    int64_t dn;                /* admitted count (pool size DN)              */
+    int32_t* x;                /* admitted positions, raster order           */
+    int32_t* y;
+    int32_t* dsum;             /* decimated block: dn * B * B values         */
+    int64_t* sum_d;            /* sum of d' over the block                  */
+    int64_t* sum_d2;           /* sum of d'^2 over the block                */
+    int64_t near_thresh;       /* positions with |H - thr| < 1e-9           */
+} or_pool;
+
+/* ------------------------------------------------------------------ */
+/* Sec. 2: the eight isometries on a B x B block, out[i][j] (row, col).  */
+/* ------------------------------------------------------------------ */
+
+/* rot: 90 degrees clockwise, out[i][j] = in[B-1-j][i]. */
+static void rot90cw(const int32_t* in, int B, int32_t* out)
+{
+    for (int i = 0; i < B; ++i)
+        for (int j = 0; j < B; ++j)
+            out[i * B + j] = in[(B - 1 - j) * B + i];
+}
+
+/* mirror: out[i][j] = in[i][B-1-j]. */
+static void mirror(const int32_t* in, int B, int32_t* out)
+{
+    for (int i = 0; i < B; ++i)
+        for (int j = 0; j < B; ++j)
+            out[i * B + j] = in[i * B + (B - 1 - j)];
+}
+
+/* T_k = rot^k for k < 4 and mirror(rot^(k-4)) for k >= 4.  B <= 32. */
+void or_isometry(const int32_t* in, int B, int k, int32_t* out)
+{
+    int32_t a[32 * 32], b[32 * 32];
+    int n = B * B;
+    memcpy(a, in, sizeof(int32_t) * n);
+    for (int r = 0; r < (k & 3); ++r) {
+        rot90cw(a, B, b);
+        memcpy(a, b, sizeof(int32_t) * n);
+    }
+    if (k >= 4) {
+        mirror(a, B, b);
+        memcpy(a, b, sizeof(int32_t) * n);
+    }
+    memcpy(out, a, sizeof(int32_t) * n);
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 2: decimated domain, B x B sums of 2x2 pixels of a 2B x 2B block. */
+/* ------------------------------------------------------------------ */
+void or_decimate(const uint8_t* img, int N, int x, int y, int B, int32_t* out)
+{
+    for (int i = 0; i < B; ++i)
+        for (int j = 0; j < B; ++j) {
+            int yy = y + 2 * i, xx = x + 2 * j;
+            out[i * B + j] = (int32_t)img[yy * N + xx] + img[yy * N + xx + 1] +
+                             img[(yy + 1) * N + xx] + img[(yy + 1) * N + xx + 1];
+        }
+}
+
+/* ------------------------------------------------------------------ */
+/* Eq. 5-6: entropy of the grey levels of a size x size block, in bits. */
+/* p_i = q_i / (number of pixels); H = -sum_i p_i log2 p_i over levels  */
+/* present, summed in ascending grey level.                            */
+/* ------------------------------------------------------------------ */
+double or_entropy_bits(const uint8_t* img, int N, int x, int y, int size)
+{
+    int64_t count[256];
+    memset(count, 0, sizeof(count));
+    for (int i = 0; i < size; ++i)
+        for (int j = 0; j < size; ++j)
+            count[img[(y + i) * N + x + j]] += 1;
+    double total = (double)size * (double)size;
+    double h = 0.0;
+    for (int g = 0; g < 256; ++g) {
+        if (count[g] == 0) continue;
+        double p = (double)count[g] / total;
+        h -= p * log2(p);
+    }
+    return h;
+}
+
+/* ------------------------------------------------------------------ */
+/* Exact error of one candidate mapping.                              */
+/*                                                                    */
+/* With d = d'/4, S = p/q and O at its optimum (eq. 3), eq. 1 becomes  */
+/*   n E = Vr - 2 S (Crd/4) + S^2 (Vd/16),                             */
+/* where Vr = n sum r^2 - (sum r)^2, Crd = n sum r d' - sum r sum d',  */
+/* Vd = n sum d'^2 - (sum d')^2.  Multiplying by 16 q^2 gives the      */
+/* integer score                                                       */
+/*   16 q^2 n E = 16 q^2 Vr - 8 p q Crd + p^2 Vd.                      */
+/* ------------------------------------------------------------------ */
+static int64_t score_from_sums(int64_t n, int64_t sr, int64_t sr2, int64_t sd,
+                               int64_t sd2, int64_t srd, int64_t p, int64_t q)
+{
+    int64_t vr = n * sr2 - sr * sr;
+    int64_t crd = n * srd - sr * sd;
+    int64_t vd = n * sd2 - sd * sd;
+    return 16 * q * q * vr - 8 * p * q * crd + p * p * vd;
+}
+
+/* Score of range r (B x B grey levels) against decimated domain dsum under
+ * isometry k and S = p/q: the domain is transformed by T_k and compared to
+ * the range pixel by pixel. */
+int64_t or_score(const int32_t* r, const int32_t* dsum, int B, int k, int p, int q)
+{
+    int32_t t[32 * 32];
+    or_isometry(dsum, B, k, t);
+    int64_t n = (int64_t)B * B, sr = 0, sr2 = 0, sd = 0, sd2 = 0, srd = 0;
+    for (int i = 0; i < n; ++i) {
+        sr += r[i];
+        sr2 += (int64_t)r[i] * r[i];
+        sd += t[i];
+        sd2 += (int64_t)t[i] * t[i];
+        srd += (int64_t)r[i] * t[i];
+    }
+    return score_from_sums(n, sr, sr2, sd, sd2, srd, p, q);
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 2 / Sec. 3: one step's domain pool.                           */
+/* ------------------------------------------------------------------ */
+void or_pool_free(or_pool* pl)
+{
+    free(pl->x); free(pl->y); free(pl->dsum); free(pl->sum_d); free(pl->sum_d2);
+    memset(pl, 0, sizeof(*pl));
+}
+
+/* Number of domain positions along one axis: x = 0, L, 2L, ... <= N - 2B. */
+int or_positions_per_axis(int N, int B, int L)
+{
+    if (N < 2 * B) return 0;
+    return (N - 2 * B) / L + 1;
+}
+
+int or_pool_build(const uint8_t* img, int N, int B, int L, double thr, or_pool* pl)
+{
+    memset(pl, 0, sizeof(*pl));
+    int per = or_positions_per_axis(N, B, L);
+    int n = B * B;
+    pl->B = B; pl->L = L; pl->n_pos = per * per;
+    pl->x = (int32_t*)malloc(sizeof(int32_t) * (size_t)(pl->n_pos ? pl->n_pos : 1));
+    pl->y = (int32_t*)malloc(sizeof(int32_t) * (size_t)(pl->n_pos ? pl->n_pos : 1));
+    if (!pl->x || !pl->y) return -1;
+    /* positions in raster order (y first, then x); admit iff H > thr. */
+    for (int iy = 0; iy < per; ++iy)
+        for (int ix = 0; ix < per; ++ix) {
+            int x = ix * L, y = iy * L;
+            int admit = 1;
+            if (thr >= 0.0) {
+                double h = or_entropy_bits(img, N, x, y, 2 * B);
+                if (fabs(h - thr) < 1e-9) pl->near_thresh += 1;
+                admit = h > thr;
+            }
+            if (admit) {
+                pl->x[pl->dn] = x;
+                pl->y[pl->dn] = y;
+                pl->dn += 1;
+            }
+        }
+    size_t cnt = (size_t)(pl->dn ? pl->dn : 1);
+    pl->dsum = (int32_t*)malloc(sizeof(int32_t) * cnt * (size_t)n);
+    pl->sum_d = (int64_t*)malloc(sizeof(int64_t) * cnt);
+    pl->sum_d2 = (int64_t*)malloc(sizeof(int64_t) * cnt);
+    if (!pl->dsum || !pl->sum_d || !pl->sum_d2) return -1;
+    for (int64_t c = 0; c < pl->dn; ++c) {
+        int32_t* d = pl->dsum + (size_t)c * n;
+        or_decimate(img, N, pl->x[c], pl->y[c], B, d);
+        int64_t s = 0, s2 = 0;
+        for (int i = 0; i < n; ++i) { s += d[i]; s2 += (int64_t)d[i] * d[i]; }
+        pl->sum_d[c] = s;
+        pl->sum_d2[c] = s2;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 2 search: best (pool index, isometry, S) for one range.        */
+/* Every pool domain, in each of the 8 isometries, at every S of the   */
+/* step; lexicographic minimum of (score, pool index, isometry, S).    */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int64_t score;
+    int64_t pool_idx;     /* -1 when the pool is empty */
+    int32_t iso, s_idx;
+} or_best;
+
+static void read_block(const uint8_t* img, int N, int x, int y, int B, int32_t* r)
+{
+    for (int i = 0; i < B; ++i)
+        for (int j = 0; j < B; ++j)
+            r[i * B + j] = img[(y + i) * N + x + j];
+}
+
+static or_best search_range(const uint8_t* img, int N, int rx, int ry,
+                            const or_pool* pl, const or_sset* ss)
+{
+    int B = pl->B, n = B * B;
+    int32_t r[32 * 32], t[32 * 32];
+    read_block(img, N, rx, ry, B, r);
+    int64_t sr = 0, sr2 = 0;
+    for (int i = 0; i < n; ++i) { sr += r[i]; sr2 += (int64_t)r[i] * r[i]; }
+    or_best best = { INT64_MAX, -1, 0, 0 };
+    for (int64_t c = 0; c < pl->dn; ++c) {
+        const int32_t* d = pl->dsum + (size_t)c * n;
+        for (int k = 0; k < 8; ++k) {
+            or_isometry(d, B, k, t);
+            int64_t srd = 0;
+            for (int i = 0; i < n; ++i) srd += (int64_t)r[i] * t[i];
+            for (int s = 0; s < ss->n_s; ++s) {
+                int64_t sc = score_from_sums(n, sr, sr2, pl->sum_d[c], pl->sum_d2[c],
+                                             srd, ss->p[s], ss->q);
+                /* strict "<": candidates arrive in increasing (c, k, s). */
+                if (sc < best.score) {
+                    best.score = sc; best.pool_idx = c; best.iso = k; best.s_idx = s;
+                }
+            }
+        }
+    }
+    return best;
+}
+
+/* Exported single-range search (used for sampled checks and timing). */
+int or_search_range(const uint8_t* img, int N, int rx, int ry, const or_pool* pl,
+                    const or_sset* ss, int64_t* score, int64_t* pool_idx,
+                    int32_t* iso, int32_t* s_idx)
+{
+    or_best b = search_range(img, N, rx, ry, pl, ss);
+    *score = b.score; *pool_idx = b.pool_idx; *iso = b.iso; *s_idx = b.s_idx;
+    return 0;
+}
+
+/* Many ranges at once, parallel over ranges (results are per range, so the
+ * thread count changes nothing but speed). */
+int or_search_ranges(const uint8_t* img, int N, int64_t count, const int32_t* rxs,
+                     const int32_t* rys, const or_pool* pl, const or_sset* ss,
+                     int nthreads, int64_t* score, int64_t* pool_idx, int32_t* iso,
+                     int32_t* s_idx)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t i = 0; i < count; ++i) {
+        or_best b = search_range(img, N, rxs[i], rys[i], pl, ss);
+        score[i] = b.score; pool_idx[i] = b.pool_idx; iso[i] = b.iso; s_idx[i] = b.s_idx;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 2 quadtree: encode one block, recursing into TL, TR, BL, BR.   */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    or_code* v;
+    int64_t n, cap;
+} code_list;
+
+static int push_code(code_list* cl, const or_code* c)
+{
+    if (cl->n == cl->cap) {
+        int64_t nc = cl->cap ? 2 * cl->cap : 64;
+        or_code* nv = (or_code*)realloc(cl->v, sizeof(or_code) * (size_t)nc);
+        if (!nv) return -1;
+        cl->v = nv; cl->cap = nc;
+    }
+    cl->v[cl->n++] = *c;
+    return 0;
+}
+
+typedef struct {
+    const uint8_t* img;
+    int N, n_levels, e16;
+    const or_pool* pools;     /* one per level */
+    const or_sset* ss;        /* one per level */
+    int64_t* ranges_searched; /* per level, atomically updated */
+} enc_ctx;
+
+static int encode_block(const enc_ctx* e, int x, int y, int level, code_list* out)
+{
+    const or_pool* pl = &e->pools[level];
+    const or_sset* ss = &e->ss[level];
+    int B = pl->B;
+    int64_t n = (int64_t)B * B;
+    int last = (level == e->n_levels - 1);
+    int64_t sr = 0;
+    for (int i = 0; i < B; ++i)
+        for (int j = 0; j < B; ++j) sr += e->img[(y + i) * e->N + x + j];
+    int64_t oq = sr / (2 * n);
+    if (oq > 127) oq = 127;
+
+    int split = 0;
+    if (pl->dn == 0) {
+        if (!last) {
+            split = 1;
+        } else {
+            or_code c = { x, y, level, B, 0, -1, (int32_t)oq, 0, 0, 0xFFFFFFFFu, 0 };
+            return push_code(out, &c);
+        }
+    } else {
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+        e->ranges_searched[level] += 1;
+        or_best b = search_range(e->img, e->N, x, y, pl, ss);
+        /* RMS error sqrt(E/n) > tol  <=>  256 * score > 16 q^2 n^2 e16^2 */
+        int64_t q = ss->q;
+        split = !last && (256 * b.score > 16 * q * q * n * n * (int64_t)e->e16 * e->e16);
+        if (!split) {
+            or_code c = { x, y, level, B, b.iso, b.s_idx, (int32_t)oq,
+                          pl->x[b.pool_idx], pl->y[b.pool_idx], (uint32_t)b.pool_idx,
+                          b.score };
+            return push_code(out, &c);
+        }
+    }
+    int h = B / 2;
+    if (encode_block(e, x, y, level + 1, out)) return -1;         /* TL */
+    if (encode_block(e, x + h, y, level + 1, out)) return -1;     /* TR */
+    if (encode_block(e, x, y + h, level + 1, out)) return -1;     /* BL */
+    return encode_block(e, x + h, y + h, level + 1, out);         /* BR */
+}
+
+/* Per-level counters reported beside the codes. */
+typedef struct {
+    int32_t n_levels;
+    int64_t pool_size[OR_MAX_LEVELS];
+    int64_t ranges[OR_MAX_LEVELS];      /* ranges searched at the level */
+    int64_t near_thresh[OR_MAX_LEVELS];
+} or_stats;
+
+/* Full encoder.  Returns 0, or -1 on bad arguments / allocation failure,
+ * or -2 when cap is too small (n_out then holds the needed count). */
+int or_encode(const uint8_t* img, int N, int B_max, int B_min, int L, double thr,
+              const or_sset* ss, double tol, int nthreads, or_code* out,
+              int64_t cap, int64_t* n_out, or_stats* st)
+{
+    if (N <= 0 || B_max < B_min || B_min < 1 || L < 1 || B_max > 32) return -1;
+    if (N % B_max) return -1;
+    int n_levels = 0;
+    for (int b = B_max; b >= B_min; b /= 2) {
+        if (b % 2 && b != B_min) return -1;
+        ++n_levels;
+        if (b == B_min) break;
+    }
+    if ((B_max >> (n_levels - 1)) != B_min || n_levels > OR_MAX_LEVELS) return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    or_pool pools[OR_MAX_LEVELS];
+    memset(pools, 0, sizeof(pools));
+    for (int l = 0; l < n_levels; ++l)
+        if (or_pool_build(img, N, B_max >> l, L, thr, &pools[l])) return -1;
+
+    int64_t searched[OR_MAX_LEVELS] = { 0 };
+    enc_ctx e = { img, N, n_levels, (int)lround(16.0 * tol), pools, ss, searched };
+    int tops = N / B_max;
+    int64_t n_top = (int64_t)tops * tops;
+    code_list* lists = (code_list*)calloc((size_t)n_top, sizeof(code_list));
+    int fail = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t t = 0; t < n_top; ++t) {
+        int x = (int)(t % tops) * B_max, y = (int)(t / tops) * B_max;
+        if (encode_block(&e, x, y, 0, &lists[t])) fail = 1;
+    }
+    int64_t total = 0;
+    for (int64_t t = 0; t < n_top; ++t) total += lists[t].n;
+    *n_out = total;
+    int rc = fail ? -1 : (total > cap ? -2 : 0);
+    if (rc == 0) {
+        int64_t k = 0;
+        for (int64_t t = 0; t < n_top; ++t) {
+            memcpy(out + k, lists[t].v, sizeof(or_code) * (size_t)lists[t].n);
+            k += lists[t].n;
+        }
+    }
+    for (int64_t t = 0; t < n_top; ++t) free(lists[t].v);
+    free(lists);
+    if (st) {
+        memset(st, 0, sizeof(*st));
+        st->n_levels = n_levels;
+        for (int l = 0; l < n_levels; ++l) {
+            st->pool_size[l] = pools[l].dn;
+            st->ranges[l] = searched[l];
+            st->near_thresh[l] = pools[l].near_thresh;
+        }
+    }
+    for (int l = 0; l < n_levels; ++l) or_pool_free(&pools[l]);
+    return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Decoder (Sec. 2: each range rebuilt from its domain and mapping).   */
+/* Integer form of r^ = (2 o_q + 1) + S (d - mean(d)), d = T(d')/4,    */
+/* rounded half up and clamped to [0, 255].                            */
+/* ------------------------------------------------------------------ */
+static void apply_code(const or_code* c, const or_sset* ss, const uint8_t* src,
+                       int N, uint8_t* dst)
+{
+    int B = c->B;
+    int64_t n = (int64_t)B * B;
+    if (c->s_idx < 0) {
+        for (int i = 0; i < B; ++i)
+            for (int j = 0; j < B; ++j)
+                dst[(c->ry + i) * N + c->rx + j] = (uint8_t)(2 * c->o_q + 1);
+        return;
+    }
+    int32_t d[32 * 32], t[32 * 32];
+    or_decimate(src, N, c->dx, c->dy, B, d);
+    or_isometry(d, B, c->iso, t);
+    int64_t sd = 0;
+    for (int i = 0; i < n; ++i) sd += d[i];
+    int64_t p = ss[c->level].p[c->s_idx], q = ss[c->level].q;
+    int64_t den = 4 * q * n;
+    for (int i = 0; i < B; ++i)
+        for (int j = 0; j < B; ++j) {
+            int64_t num = (2 * (int64_t)c->o_q + 1) * den + p * (n * t[i * B + j] - sd) + den / 2;
+            int64_t v = num >= 0 ? num / den : -((-num + den - 1) / den);  /* floor */
+            if (v < 0) v = 0;
+            if (v > 255) v = 255;
+            dst[(c->ry + i) * N + c->rx + j] = (uint8_t)v;
+        }
+}
+
+int or_decode(const or_code* codes, int64_t n_codes, const or_sset* ss, int N,
+              int iters_max, uint8_t* out, int* iters_used)
+{
+    size_t npx = (size_t)N * N;
+    uint8_t* cur = (uint8_t*)malloc(npx);
+    uint8_t* nxt = (uint8_t*)malloc(npx);
+    if (!cur || !nxt) { free(cur); free(nxt); return -1; }
+    memset(cur, 128, npx);
+    int it = 0;
+    for (; it < iters_max; ++it) {
+        memcpy(nxt, cur, npx);
+        for (int64_t i = 0; i < n_codes; ++i) apply_code(&codes[i], ss, cur, N, nxt);
+        int same = memcmp(nxt, cur, npx) == 0;
+        uint8_t* tmp = cur; cur = nxt; nxt = tmp;
+        if (same) { ++it; break; }
+    }
+    memcpy(out, cur, npx);
+    *iters_used = it;
+    free(cur); free(nxt);
+    return 0;
+}
+
+/* Eq. 4: PSNR in dB between two N x N images (infinity when identical). */
+double or_psnr(const uint8_t* a, const uint8_t* b, int64_t npx)
+{
+    double se = 0.0;
+    for (int64_t i = 0; i < npx; ++i) {
+        double d = (double)a[i] - (double)b[i];
+        se += d * d;
+    }
+    if (se == 0.0) return INFINITY;
+    return 10.0 * log10(255.0 * 255.0 / (se / (double)npx));
+}
+
+/* Eq. 8: address width X = ceil(log2 DN) bits. */
+int or_address_bits(int64_t dn)
+{
+    int x = 0;
+    while (((int64_t)1 << x) < dn) ++x;
+    return x;
+}
+
+int or_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
