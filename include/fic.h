@@ -1,0 +1,221 @@
+/*
+ * fic.h -- C ABI of the GB300 (sm_103a) range-domain block search of the
+ * modified fast fractal image encoder (Salarian & Miar Naimi, arXiv
+ * 1502.00324).
+ *
+ * What one encode computes (paper section in brackets):
+ *   - ranges: non-overlapping B x B blocks of the N x N grey image, stored
+ *     left to right, top to bottom [Sec. 2, Sec. 3.3];
+ *   - domains: every 2B x 2B block at integer step L in x and y, decimated
+ *     2x2 before comparison [Sec. 2]; the pool keeps the domains whose
+ *     grey-level entropy is greater than a threshold [Abstract, Sec. 3,
+ *     eq. 5-6];
+ *   - for every range: every pool domain in each of the 8 isometries (0, 90,
+ *     180, 270 degrees clockwise, and each mirrored) [Sec. 2], at each
+ *     predefined contrast factor S of the step [Sec. 3.2], with the
+ *     least-squares optimal offset O [eq. 3], scored by eq. 1; the best
+ *     mapping is kept;
+ *   - quadtree steps: a range whose RMS error exceeds the tolerance splits
+ *     into four children for the next, smaller step; the last step stores
+ *     its best mapping regardless [Sec. 2].
+ *
+ * Exactness: decimated domains are carried as 2x2 SUMS d' (0..1020) and
+ * S = p/q, so 16 q^2 n E(S, O*) = 16 q^2 Vr - 8 p q Crd + p^2 Vd is an
+ * exact integer (n = B*B, Vr = n sum r^2 - (sum r)^2,
+ * Crd = n sum r d' - sum r sum d', Vd = n sum d'^2 - (sum d')^2).  Selection
+ * is the lexicographic minimum of (score, pool index, isometry, S index);
+ * the codes are therefore bit-exact across engines and against a CPU
+ * reference.
+ *
+ * Memory and threads: every entry point is host-callable and synchronous
+ * with respect to the host (it returns when its results are written).  GPU
+ * work runs on the given CUDA stream (NULL = legacy default stream) of the
+ * current device.  Pointers documented "host or device" are classified with
+ * cudaPointerGetAttributes.  The library keeps one workspace per device and
+ * context; calls that share a context must not overlap in time.
+ *
+ * Errors: every int-returning call returns FIC_OK (0) or a negative FIC_E*
+ * code; fic_strerror() names it.  No call aborts the process.
+ */
+#ifndef FIC_H
+#define FIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ */
+/* Status codes                                                        */
+/* ------------------------------------------------------------------ */
+#define FIC_OK 0
+#define FIC_EINVAL (-1)   /* bad argument: N % B_max != 0, B_min > B_max,
+                             B not a power of two in {2,4,8,16}, L < 1,
+                             err_tol outside [0, 255], bad S set (n_s < 1
+                             or > FIC_MAX_S, q < 1 or > 256, p < 0 or
+                             p > q), NULL pointer                         */
+#define FIC_ENOMEM (-2)   /* device or host allocation failed            */
+#define FIC_ECUDA (-3)    /* a CUDA runtime call or kernel failed        */
+#define FIC_ETIMEOUT (-4) /* a bounded device-side wait gave up; the
+                             kernel returned early and the context is
+                             still usable                                */
+#define FIC_EBUSY (-5)    /* server admission refused (no slot / memory) */
+#define FIC_ENODEV (-6)   /* no CUDA device, or not compute capability
+                             10.3 (sm_103a)                              */
+#define FIC_ECAP (-7)     /* caller-provided output buffer too small;
+                             the needed count is still reported           */
+#define FIC_ENOTREADY (-8)/* server ticket not finished yet              */
+
+#define FIC_MAX_LEVELS 4  /* quadtree steps: 16 -> 8 -> 4 -> 2 (Sec. 2)  */
+#define FIC_MAX_S 16      /* contrast factors per step                   */
+
+/* Contraction engine for the sum r d' term.                           */
+#define FIC_ENGINE_TENSOR 0 /* tcgen05.mma kind::f16 (FP16 in, FP32 accum),
+                               operands centred so every partial sum is an
+                               integer below 2^24 (exact)                 */
+#define FIC_ENGINE_PLAIN 1  /* CUDA-core int32 multiply-add              */
+
+/* One step's contrast factors S_i = p[i] / q (Sec. 3.2: 16x16 {0.1},
+ * 8x8 {0.2, 0.4}, 4x4 {0.3, 0.8}, 2x2 {0.5, 0.9}, i.e. q = 10). */
+typedef struct {
+    int32_t n_s;
+    int32_t q;
+    int32_t p[FIC_MAX_S];
+} fic_sset;
+
+/* One stored record per coded range (Sec. 3.3, Fig. 7).  16 bytes.
+ * Positions are explicit for checking; pool_idx is the domain address (the
+ * index in the step's domain list, Sec. 3.3, eq. 8).  The range side is
+ * B_max >> level.  s_idx == 0xFF and pool_idx == 0xFFFFFFFF mark a
+ * mean-only record (empty pool at the last step).  The decoded range mean
+ * is 2 * o_q + 1. */
+typedef struct {
+    uint16_t rx, ry;     /* range top-left, pixels                       */
+    uint16_t dx, dy;     /* domain top-left, pixels                      */
+    uint32_t pool_idx;   /* domain address                                */
+    uint8_t level;       /* quadtree step, 0 = B_max                      */
+    uint8_t iso;         /* isometry 0..7: rot^k (k<4), mirror(rot^(k-4)) */
+    uint8_t s_idx;       /* index into the step's S set                   */
+    uint8_t o_q;         /* 7-bit range mean, min(127, floor(sum r/(2n))) */
+} fic_code;
+
+/* Encode result.  Codes are ordered by top-level range in raster order,
+ * then depth-first in TL, TR, BL, BR order (the order of Sec. 3.3). */
+typedef struct {
+    fic_code* codes;                    /* host array unless the caller gave
+                                           its own buffer                    */
+    int64_t n_codes;
+    int32_t n_levels;
+    int32_t N;
+    int32_t B_max;
+    int32_t owns_codes;                 /* 1: free with fic_result_free      */
+    fic_sset S_sets[FIC_MAX_LEVELS];    /* the S sets used, for decoding     */
+    int64_t n_positions[FIC_MAX_LEVELS];/* domain positions per step         */
+    int64_t pool_size[FIC_MAX_LEVELS];  /* admitted pool size DN per step    */
+    int64_t ranges[FIC_MAX_LEVELS];     /* ranges searched per step          */
+    int64_t matches[FIC_MAX_LEVELS];    /* ranges * DN * 8 per step          */
+    int64_t near_thresh[FIC_MAX_LEVELS];/* positions with |H - thr| < 1e-9   */
+} fic_result;
+
+/* Full parameter set. */
+typedef struct {
+    int32_t N;               /* image side; N % B_max == 0                 */
+    int32_t B_max, B_min;    /* range sides, powers of two in {2,4,8,16}   */
+    int32_t L;               /* domain step >= 1                            */
+    double entropy_thresh;   /* bits; < 0 admits every domain               */
+    double err_tol;          /* RMS grey levels, quantised to 1/16          */
+    fic_sset S_sets[FIC_MAX_LEVELS]; /* one per step, B_max first          */
+    int32_t engine;          /* FIC_ENGINE_*                                */
+    int32_t reserved;        /* must be 0                                   */
+} fic_params;
+
+/* fic_encode -- encode one N x N uint8 image (row-major, pitch N).
+ *   img      host or device pointer, caller-owned, read only.
+ *   S_sets   host array, one fic_sset per quadtree step, B_max first.
+ *   err_tol  split when RMS error > err_tol (ignored when B_max == B_min).
+ *   out      host struct; out->codes is a host array allocated by the
+ *            library (free with fic_result_free).
+ *   stream   cudaStream_t or NULL.
+ * Uses the tensor-core engine.  Returns FIC_OK or FIC_E*. */
+int fic_encode(const uint8_t* img, int N, int B_max, int B_min, int L,
+               double entropy_thresh, const fic_sset* S_sets, double err_tol,
+               fic_result* out, void* stream);
+
+/* fic_encode_ex -- as fic_encode with a full parameter set and an optional
+ * caller-owned output buffer.
+ *   codes_out  NULL: the library allocates a host array (out->owns_codes=1);
+ *              else a host or device buffer of codes_cap records that
+ *              receives the codes (out->codes = codes_out).  If it is too
+ *              small the call returns FIC_ECAP with out->n_codes set. */
+int fic_encode_ex(const uint8_t* img, const fic_params* p, fic_code* codes_out,
+                  int64_t codes_cap, fic_result* out, void* stream);
+
+/* fic_decode -- rebuild the image from a result on the GPU (Sec. 2): start
+ * from a constant 128 image; each pass rebuilds every range from its domain
+ * in the previous pass, pixel = clamp(round_half_up((2 o_q + 1) +
+ * S (d - mean d)), 0, 255) with d = T_iso(d')/4; stop at a fixed point or
+ * after iters_max passes.
+ *   r          host struct from fic_encode*; r->codes host or device.
+ *   out_img    host or device, N*N bytes, caller-owned.
+ *   iters_used host, may be NULL. */
+int fic_decode(const fic_result* r, int N, int iters_max, uint8_t* out_img,
+               int* iters_used, void* stream);
+
+/* fic_domain_pool -- kernels (a) and (b) alone: entropy of every 2B x 2B
+ * domain position at step L (eq. 5-6, bits, FP64 from integer counts) and
+ * the stable raster-order list of admitted positions (Sec. 3).
+ *   pool_xy   host, 2 * cap int32 (x, y pairs); may be NULL with cap 0.
+ *   entropy   host, n_positions doubles, may be NULL.
+ *   dn, near  host outputs (near: positions with |H - thr| < 1e-9).
+ * Returns FIC_ECAP (with *dn set) when cap < DN. */
+int fic_domain_pool(const uint8_t* img, int N, int B, int L, double entropy_thresh,
+                    int32_t* pool_xy, int64_t cap, int64_t* dn, double* entropy,
+                    int64_t* near, void* stream);
+
+/* Frees the library-owned parts of a result (the code array when
+ * owns_codes).  Safe on a zeroed struct. */
+void fic_result_free(fic_result* r);
+
+/* Human-readable name of a status code (static string). */
+const char* fic_strerror(int status);
+
+/* ------------------------------------------------------------------ */
+/* Instrumentation                                                     */
+/* ------------------------------------------------------------------ */
+#define FIC_K_ENTROPY 0
+#define FIC_K_SCAN 1
+#define FIC_K_GATHER 2
+#define FIC_K_RANGE_PREP 3
+#define FIC_K_CONTRACT_TC 4
+#define FIC_K_CONTRACT_PLAIN 5
+#define FIC_K_SPLIT 6
+#define FIC_K_ORDER 7
+#define FIC_K_DECODE 8
+#define FIC_K_MISC 9
+#define FIC_K_COUNT 10
+
+typedef struct {
+    int64_t launches[FIC_K_COUNT];  /* kernel launches per kind            */
+    double ms[FIC_K_COUNT];         /* summed CUDA-event time per kind
+                                       (only while timing is enabled)      */
+    double flops[FIC_K_COUNT];      /* algorithmic flops: 2 * M * N * K of
+                                       the contraction (M = 8 ranges,
+                                       N = DN, K = B*B), summed            */
+    double bytes[FIC_K_COUNT];      /* algorithmic DRAM bytes, summed      */
+    int64_t matches;                /* (range, pool domain, isometry)      */
+} fic_stats;
+
+/* Zero the counters; enable (1) or disable (0) per-kernel CUDA-event
+ * timing.  Events are recorded on the stream each kernel runs on. */
+int fic_stats_reset(int timing);
+/* Copy the counters accumulated since the last reset. */
+int fic_stats_read(fic_stats* out);
+
+/* Library build string (compiled architectures and version). */
+const char* fic_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FIC_H */

@@ -1,0 +1,140 @@
+// contract_plain.cu -- the CUDA-core form of the search: C' = A' . D'^T with
+// int32 multiply-adds in registers, fused with the scoring epilogue.
+//
+// A' rows are (range, isometry) pairs holding T_k^-1(r) - 128 (the isometry
+// moved to the range side: sum r . T_k(d') = sum T_k^-1(r) . d', Sec. 2);
+// D' rows are pool domains holding d' - 510.  Both come in the tile layout of
+// common.cuh.  One block owns a 128-row M tile (16 ranges x 8 isometries)
+// and a chunk of 128-column tiles; thread (ty, tx) owns range ty of the tile
+// (its 8 isometry rows) and columns tx, tx+16, ..., tx+112 of each tile.
+#include "epilogue.cuh"
+#include "kernels.h"
+
+namespace fic {
+
+template <int K, int NS>
+__global__ void __launch_bounds__(256)
+contract_plain_kernel(const __half* __restrict__ A, int64_t rows_pad,
+                      const __half* __restrict__ D, int64_t cols_pad,
+                      const float* __restrict__ cf, const ColExact* __restrict__ ci,
+                      const RowConst* __restrict__ rc, int R, int dn, int ctiles_per_chunk,
+                      int n_ctiles, int n_chunks, Best* __restrict__ part,
+                      const __grid_constant__ StepParams sp)
+{
+    __shared__ __align__(16) int sA[16][128];
+    __shared__ __align__(16) int sD[16][128];
+    const int tid = threadIdx.x;
+    const int ty = tid >> 4, tx = tid & 15;
+    const int mtile = blockIdx.y, chunk = blockIdx.x;
+    const int range = mtile * kRangesPerTile + ty;
+    const bool valid = range < R;
+    RowConst r = valid ? rc[range] : RowConst{0, 0, 0.f, 0.f};
+    const float inv_n = 1.0f / (float)sp.n;
+
+    RowState st[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) row_state_init(st[i]);
+
+    const int ct0 = chunk * ctiles_per_chunk;
+    const int ct1 = min(n_ctiles, ct0 + ctiles_per_chunk);
+    const int lrow = tid & 127, lkg = tid >> 7;
+
+    for (int ct = ct0; ct < ct1; ++ct) {
+        int acc[8][8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = 0;
+
+#pragma unroll 1
+        for (int kc = 0; kc < K / 16; ++kc) {
+            const int k0 = kc * 16 + lkg * 8;
+            const uint4 va = *reinterpret_cast<const uint4*>(
+                A + tile_off((int64_t)mtile * kMTile + lrow, k0, rows_pad, K));
+            const uint4 vd = *reinterpret_cast<const uint4*>(
+                D + tile_off((int64_t)ct * 128 + lrow, k0, cols_pad, K));
+            const __half* ha = reinterpret_cast<const __half*>(&va);
+            const __half* hd = reinterpret_cast<const __half*>(&vd);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                sA[lkg * 8 + e][lrow] = __half2int_rn(ha[e]);
+                sD[lkg * 8 + e][lrow] = __half2int_rn(hd[e]);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const int4 a0 = *reinterpret_cast<const int4*>(&sA[k][ty * 8]);
+                const int4 a1 = *reinterpret_cast<const int4*>(&sA[k][ty * 8 + 4]);
+                const int av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                int dv[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) dv[j] = sD[k][tx + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] += av[i] * dv[j];
+            }
+            __syncthreads();
+        }
+        if (valid) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                float x[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) x[j] = (float)acc[i][j];
+                epi_block<NS, 8>(st[i], x, cf, ct * 128 + tx, ct * 128 + tx, 16, (unsigned)i, r.a,
+                                 r.delta, inv_n, r.sr, ci, dn, &sp);
+            }
+        }
+    }
+    // best over the 8 isometries held by this thread, then over the 16 threads
+    long long h = st[0].h;
+    unsigned idx = st[0].idx;
+#pragma unroll
+    for (int i = 1; i < 8; ++i)
+        if (key_less(st[i].h, st[i].idx, h, idx)) {
+            h = st[i].h;
+            idx = st[i].idx;
+        }
+#pragma unroll
+    for (int m = 1; m < 16; m <<= 1) key_min_shfl(h, idx, m);
+    if (tx == 0 && valid) {
+        Best b;
+        b.h = h;
+        b.idx = idx;
+        b.pad = 0;
+        part[(int64_t)range * n_chunks + chunk] = b;
+    }
+}
+
+template <int K>
+static cudaError_t launch_plain_k(const ContractArgs& a, cudaStream_t s)
+{
+    dim3 grid(a.n_chunks, a.rows_pad / kMTile);
+    const int n_ctiles = (int)(a.cols_pad / 128);
+    const int per = a.ctiles_per_chunk;
+#define FIC_PLAIN_CASE(NSV)                                                              \
+    contract_plain_kernel<K, NSV><<<grid, 256, 0, s>>>(                                  \
+        a.A, a.rows_pad, a.D, a.cols_pad, a.cf, a.ci, a.rc, a.R, a.dn, per, n_ctiles,   \
+        a.n_chunks, a.part, a.sp)
+    switch (a.sp.ns) {
+        case 1: FIC_PLAIN_CASE(1); break;
+        case 2: FIC_PLAIN_CASE(2); break;
+        case 3: FIC_PLAIN_CASE(3); break;
+        default: FIC_PLAIN_CASE(0); break;
+    }
+#undef FIC_PLAIN_CASE
+    return cudaGetLastError();
+}
+
+cudaError_t launch_contract_plain(const ContractArgs& a, cudaStream_t s)
+{
+    switch (a.K) {
+        case 16: return launch_plain_k<16>(a, s);
+        case 64: return launch_plain_k<64>(a, s);
+        case 256: return launch_plain_k<256>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace fic

@@ -1,0 +1,507 @@
+// contract_tc.cu -- the tensor-core form of the search on sm_103a:
+// C' = A' . D'^T on tcgen05 (kind::f16, FP16 operands, FP32 accumulators in
+// tensor memory), fused with the exact scoring/argmin epilogue.
+//
+// A' rows: (range, isometry) pairs holding T_k^-1(r) - 128 (the isometry is
+// applied on the range side because sum d' and sum d'^2 are isometry
+// invariant and sum r . T_k(d') = sum T_k^-1(r) . d', Sec. 2); D' rows: pool
+// domains holding d' - 510.  With |r - 128| <= 128, |d' - 510| <= 510 and
+// n <= 256 terms every partial sum is an integer below 2^24, so the FP32
+// accumulators hold C' exactly.
+//
+// One persistent CTA per SM walks work items (128-row M tile, chunk of
+// 256-column N tiles).  Warp roles:
+//   warp 0      one thread issues bulk async copies (the TMA engine): the
+//               A tile once per item, then per N tile its column constants
+//               and its K-blocks of D' into a ring of shared-memory stages;
+//   warp 1      allocates 512 TMEM columns (two 128 x 256 FP32
+//               accumulators); one thread issues tcgen05.mma per K step and
+//               tcgen05.commit to release stages and publish accumulators;
+//   warps 2-9   epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (one
+//               row per thread) for one half of the 256 columns with
+//               tcgen05.ld, runs the filter/exact argmin of epilogue.cuh,
+//               and releases the accumulator.
+// Every mbarrier wait is bounded (globaltimer); on expiry the kernel records
+// FIC_ETIMEOUT in the error word, drains its own copies and MMAs, frees TMEM
+// and returns.
+#include <cstdio>
+
+#include "epilogue.cuh"
+#include "kernels.h"
+
+namespace fic {
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s: far above any stage wait
+constexpr uint64_t kDrainNs = 100000000ull;  // 0.1 s for the drain after an error
+
+// Bounded parity wait.  Returns false when the limit passed or another
+// thread already recorded an error.
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, uint64_t limit)
+{
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_try(bar, parity)) return true;
+        if ((i & 63) == 0) {
+            if (*(volatile int*)err) return false;
+            if (global_ns() - t0 > limit) {
+                atomicCAS(err, 0, kErrTimeout);
+                return false;
+            }
+        }
+    }
+}
+
+// Bulk async copy global -> shared (the TMA engine, non-tensor form),
+// completing on an mbarrier.  Addresses 16-byte aligned, size % 16 == 0.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before()
+{
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after()
+{
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(bar)
+                 : "memory");
+}
+
+// D[tmem] (+)= A[smem] . B[smem]^T, M = 128, N = 256, K = 16.
+__device__ __forceinline__ void tc_mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                           uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// 32 lanes x 32 consecutive FP32 columns; thread i gets lane (base lane + i).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    // the wait takes the registers as operands so no use moves above it
+    asm volatile(
+        "tcgen05.wait::ld.sync.aligned;"
+        : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+          "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]),
+          "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]),
+          "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]),
+          "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]),
+          "+r"(r[31])
+        :
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor, K-major, no swizzle: start address,
+// leading (K-direction core matrix) and stride (8-row group) byte offsets,
+// descriptor version 1 at bits 46-47.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = F16,
+// both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N)
+{
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+constexpr int kThreads = 320;
+constexpr int kEpiWarps = 8;
+constexpr uint32_t kTmemCols = 512;
+
+struct TcParams {
+    const __half* A;
+    int64_t rows_pad;
+    const __half* D;
+    int64_t cols_pad;
+    const float* cf;
+    const ColExact* ci;
+    const RowConst* rc;
+    Best* part;
+    int* err;
+    int R, dn, n_chunks, per_chunk, n_ct, n_items, nstage;
+};
+
+template <int K, int NS>
+__global__ void __launch_bounds__(kThreads, 1)
+contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ StepParams sp)
+{
+    constexpr int KB = K < 64 ? K : 64;
+    constexpr int NKB = K / KB;
+    constexpr uint32_t kAKBBytes = 128u * KB * 2u;     // one K-block of the A tile
+    constexpr uint32_t kBStageBytes = 256u * KB * 2u;  // one K-block of a D tile
+    constexpr uint32_t kSbo = KB * 16u;                // 8-row group stride
+    constexpr uint32_t kIdesc = idesc_f16_f32(128, 256);
+    const uint32_t cf_bytes = 256u * (uint32_t)sp.cw * 4u;
+    const int nstage = P.nstage;
+
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* sA = smem;
+    uint8_t* sB = sA + NKB * kAKBBytes;
+    uint8_t* sCF = sB + (size_t)nstage * kBStageBytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sCF + 2 * cf_bytes);
+    // barrier slots
+    const uint32_t b_base = smem_u32(bars);
+    const uint32_t a_full = b_base, a_empty = b_base + 8;
+    auto full = [&](int s) { return b_base + 16 + 8u * s; };
+    auto empty = [&](int s) { return b_base + 16 + 8u * (nstage + s); };
+    const uint32_t b_tail = b_base + 16 + 16u * nstage;
+    auto tfull = [&](int a) { return b_tail + 8u * a; };
+    auto tempty = [&](int a) { return b_tail + 16 + 8u * a; };
+    auto cff = [&](int a) { return b_tail + 32 + 8u * a; };
+    auto cfe = [&](int a) { return b_tail + 48 + 8u * a; };
+    const uint32_t drain = b_tail + 64;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 + 2 * nstage + 9);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        mbar_init(a_full, 1);
+        mbar_init(a_empty, 1);
+        for (int s = 0; s < nstage; ++s) {
+            mbar_init(full(s), 1);
+            mbar_init(empty(s), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(tfull(a), 1);
+            mbar_init(tempty(a), kEpiWarps);
+            mbar_init(cff(a), 1);
+            mbar_init(cfe(a), kEpiWarps);
+        }
+        mbar_init(drain, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(tmem_slot)), "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    int* err = P.err;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            int64_t it = 0, tcount = 0, icount = 0;
+            bool ok = true;
+            for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
+                const int mtile = item / P.n_chunks, chunk = item % P.n_chunks;
+                const int ct0 = chunk * P.per_chunk;
+                const int ct1 = min(P.n_ct, ct0 + P.per_chunk);
+                if (!(ok = mbar_wait(a_empty, (uint32_t)((icount & 1) ^ 1), err, kWaitNs))) break;
+                mbar_expect_tx(a_full, NKB * kAKBBytes);
+                for (int kb = 0; kb < NKB; ++kb)
+                    bulk_g2s(smem_u32(sA + kb * kAKBBytes),
+                             P.A + ((int64_t)kb * P.rows_pad * KB + (int64_t)mtile * 128 * KB),
+                             kAKBBytes, a_full);
+                ++icount;
+                for (int ct = ct0; ct < ct1 && ok; ++ct) {
+                    const int acc = (int)(tcount & 1);
+                    const uint32_t ph = (uint32_t)((tcount >> 1) & 1);
+                    if (!(ok = mbar_wait(cfe(acc), ph ^ 1, err, kWaitNs))) break;
+                    mbar_expect_tx(cff(acc), cf_bytes);
+                    bulk_g2s(smem_u32(sCF + acc * cf_bytes), P.cf + (int64_t)ct * 256 * sp.cw,
+                             cf_bytes, cff(acc));
+                    for (int kb = 0; kb < NKB; ++kb) {
+                        const int s = (int)(it % nstage);
+                        const uint32_t sph = (uint32_t)((it / nstage) & 1);
+                        if (!(ok = mbar_wait(empty(s), sph ^ 1, err, kWaitNs))) break;
+                        mbar_expect_tx(full(s), kBStageBytes);
+                        bulk_g2s(smem_u32(sB + (size_t)s * kBStageBytes),
+                                 P.D + ((int64_t)kb * P.cols_pad * KB + (int64_t)ct * 256 * KB),
+                                 kBStageBytes, full(s));
+                        ++it;
+                    }
+                    ++tcount;
+                }
+            }
+            if (!ok) {
+                // drain: let every copy this thread armed land before exit
+                for (int64_t j = (it > nstage ? it - nstage : 0); j < it; ++j)
+                    mbar_wait(full((int)(j % nstage)), (uint32_t)((j / nstage) & 1), err + 1,
+                              kDrainNs);
+                if (icount > 0) mbar_wait(a_full, (uint32_t)((icount - 1) & 1), err + 1, kDrainNs);
+                for (int64_t j = (tcount > 2 ? tcount - 2 : 0); j < tcount; ++j)
+                    mbar_wait(cff((int)(j & 1)), (uint32_t)((j >> 1) & 1), err + 1, kDrainNs);
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            int64_t it = 0, tcount = 0, icount = 0;
+            bool ok = true;
+            for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
+                const int chunk = item % P.n_chunks;
+                const int ct0 = chunk * P.per_chunk;
+                const int ct1 = min(P.n_ct, ct0 + P.per_chunk);
+                if (!(ok = mbar_wait(a_full, (uint32_t)(icount & 1), err, kWaitNs))) break;
+                tc_fence_after();
+                for (int ct = ct0; ct < ct1 && ok; ++ct) {
+                    const int acc = (int)(tcount & 1);
+                    const uint32_t ph = (uint32_t)((tcount >> 1) & 1);
+                    if (!(ok = mbar_wait(tempty(acc), ph ^ 1, err, kWaitNs))) break;
+                    tc_fence_after();
+                    const uint32_t d_tmem = tmem_base + (uint32_t)acc * 256u;
+                    for (int kb = 0; kb < NKB; ++kb) {
+                        const int s = (int)(it % nstage);
+                        const uint32_t sph = (uint32_t)((it / nstage) & 1);
+                        if (!(ok = mbar_wait(full(s), sph, err, kWaitNs))) break;
+                        tc_fence_after();
+                        const uint32_t a0 = smem_u32(sA + kb * kAKBBytes);
+                        const uint32_t b0 = smem_u32(sB + (size_t)s * kBStageBytes);
+#pragma unroll
+                        for (int j = 0; j < KB / 16; ++j)
+                            tc_mma_f16(d_tmem, smem_desc(a0 + 256u * j, 128u, kSbo),
+                                       smem_desc(b0 + 256u * j, 128u, kSbo), kIdesc,
+                                       (kb | j) != 0 ? 1u : 0u);
+                        tc_commit(empty(s));
+                        ++it;
+                    }
+                    if (!ok) break;
+                    tc_commit(tfull(acc));
+                    ++tcount;
+                }
+                if (!ok) break;
+                tc_commit(a_empty);
+                ++icount;
+            }
+            // every issued MMA has finished before TMEM is released
+            tc_commit(drain);
+            mbar_wait(drain, 0, err + 1, kWaitNs);
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int e = warp - 2;
+        const int quad = warp & 3;
+        const int hsel = e >> 2;
+        const float inv_n = 1.0f / (float)sp.n;
+        int64_t tcount = 0;
+        bool ok = true;
+        for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
+            const int mtile = item / P.n_chunks, chunk = item % P.n_chunks;
+            const int ct0 = chunk * P.per_chunk;
+            const int ct1 = min(P.n_ct, ct0 + P.per_chunk);
+            const int row = mtile * 128 + quad * 32 + lane;
+            const int range = row >> 3;
+            const unsigned iso = (unsigned)(row & 7);
+            const bool valid = range < P.R;
+            const RowConst r = valid ? P.rc[range] : RowConst{0, 0, 0.f, 0.f};
+            RowState st;
+            row_state_init(st);
+            for (int ct = ct0; ct < ct1; ++ct) {
+                const int acc = (int)(tcount & 1);
+                const uint32_t ph = (uint32_t)((tcount >> 1) & 1);
+                if (!(ok = mbar_wait(tfull(acc), ph, err, kWaitNs))) break;
+                if (!(ok = mbar_wait(cff(acc), ph, err, kWaitNs))) break;
+                tc_fence_after();
+                const float* cfs = reinterpret_cast<const float*>(sCF + acc * cf_bytes);
+#pragma unroll 1
+                for (int cb = 0; cb < 4; ++cb) {
+                    const int cit = hsel * 128 + cb * 32;
+                    float x[32];
+                    __syncwarp();
+                    tmem_ld32(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * 256 + cit),
+                              x);
+                    if (valid)
+                        epi_block<NS, 32>(st, x, cfs, cit, ct * 256 + cit, 1, iso, r.a, r.delta,
+                                          inv_n, r.sr, P.ci, P.dn, &sp);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(tempty(acc));
+                    mbar_arrive(cfe(acc));
+                }
+                ++tcount;
+            }
+            if (!ok) break;
+            // best over the 8 isometries of each range (lanes 8j .. 8j+7)
+            long long h = st.h;
+            unsigned idx = st.idx;
+            key_min_shfl(h, idx, 1);
+            key_min_shfl(h, idx, 2);
+            key_min_shfl(h, idx, 4);
+            if (valid && (lane & 7) == 0) {
+                Best b;
+                b.h = h;
+                b.idx = idx;
+                b.pad = 0;
+                P.part[(int64_t)range * (2 * P.n_chunks) + 2 * chunk + hsel] = b;
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                     "r"(kTmemCols)
+                     : "memory");
+    }
+}
+
+constexpr size_t kSmemBudget = 220 * 1024;
+constexpr size_t kSmemMinForOneCta = 120 * 1024;  // > half an SM: one CTA per SM
+
+template <int K>
+size_t tc_layout(int cw, int* nstage_out)
+{
+    constexpr int KB = K < 64 ? K : 64;
+    const size_t a_bytes = (size_t)128 * K * 2;
+    const size_t stage = (size_t)256 * KB * 2;
+    const size_t cf = (size_t)2 * 256 * cw * 4;
+    const size_t fixed = a_bytes + cf + 1024;
+    int ns = (int)((kSmemBudget - fixed) / stage);
+    if (ns > 8) ns = 8;
+    if (ns < 2) ns = 2;
+    *nstage_out = ns;
+    size_t total = fixed + (size_t)ns * stage;
+    if (total < kSmemMinForOneCta) total = kSmemMinForOneCta;
+    return total;
+}
+
+template <int K, int NS>
+cudaError_t launch_tc_kns(const ContractArgs& a, cudaStream_t s)
+{
+    int nstage = 0;
+    const size_t smem = tc_layout<K>(a.sp.cw, &nstage);
+    auto kern = contract_tc_kernel<K, NS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    TcParams P;
+    P.A = a.A;
+    P.rows_pad = a.rows_pad;
+    P.D = a.D;
+    P.cols_pad = a.cols_pad;
+    P.cf = a.cf;
+    P.ci = a.ci;
+    P.rc = a.rc;
+    P.part = a.part;
+    P.err = a.err;
+    P.R = a.R;
+    P.dn = a.dn;
+    P.n_chunks = a.n_chunks;
+    P.per_chunk = a.ctiles_per_chunk;
+    P.n_ct = (int)(a.cols_pad / 256);
+    P.n_items = (int)(a.rows_pad / 128) * a.n_chunks;
+    P.nstage = nstage;
+    const int grid = P.n_items < a.grid_ctas ? P.n_items : a.grid_ctas;
+    kern<<<grid, kThreads, smem, s>>>(P, a.sp);
+    return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t launch_tc_k(const ContractArgs& a, cudaStream_t s)
+{
+    switch (a.sp.ns) {
+        case 1: return launch_tc_kns<K, 1>(a, s);
+        case 2: return launch_tc_kns<K, 2>(a, s);
+        case 3: return launch_tc_kns<K, 3>(a, s);
+        default: return launch_tc_kns<K, 0>(a, s);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_contract_tc(const ContractArgs& a, cudaStream_t s)
+{
+    switch (a.K) {
+        case 16: return launch_tc_k<16>(a, s);
+        case 64: return launch_tc_k<64>(a, s);
+        case 256: return launch_tc_k<256>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+size_t contract_tc_smem_bytes(int K)
+{
+    int ns = 0;
+    switch (K) {
+        case 16: return tc_layout<16>(4, &ns);
+        case 64: return tc_layout<64>(4, &ns);
+        case 256: return tc_layout<256>(4, &ns);
+        default: return 0;
+    }
+}
+
+}  // namespace fic

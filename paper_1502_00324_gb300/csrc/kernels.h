@@ -1,0 +1,81 @@
+// kernels.h -- host-side launch interface of the search kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace fic {
+
+// Arguments of one contraction + scoring launch (one quadtree step).
+struct ContractArgs {
+    const __half* A;      // ranges x isometries, tile layout, rows_pad rows
+    int64_t rows_pad;     // multiple of 128
+    const __half* D;      // pool domains, tile layout, cols_pad rows
+    int64_t cols_pad;     // multiple of 256
+    int K;                // 16, 64 or 256
+    const float* cf;      // column filter constants, cols_pad * sp.cw floats
+    const ColExact* ci;   // exact column sums, cols_pad entries
+    const RowConst* rc;   // per active range
+    int R;                // active ranges
+    int dn;               // pool size
+    int n_chunks;         // column chunks per M tile
+    int ctiles_per_chunk; // column tiles per chunk (128 wide for the plain
+                          // engine, 256 wide for the tensor engine)
+    Best* part;           // R * n_chunks partial bests
+    StepParams sp;
+    int* err;             // device error word
+    int grid_ctas;        // persistent grid size (tensor engine)
+};
+
+cudaError_t launch_contract_plain(const ContractArgs& a, cudaStream_t s);
+cudaError_t launch_contract_tc(const ContractArgs& a, cudaStream_t s);
+size_t contract_tc_smem_bytes(int K);
+
+// Step kernels (stages.cu).
+cudaError_t launch_entropy_table(double* T, int count, cudaStream_t s);
+cudaError_t launch_entropy(const uint8_t* img, int N, int B, int L, int per, double thr,
+                           const double* T, uint32_t* flags, double* H,
+                           unsigned long long* near, cudaStream_t s);
+// Exclusive scan of n uint32 values; *total receives the sum.  tmp holds at
+// least scan_tmp_words(n) words.
+int64_t scan_tmp_words(int64_t n);
+cudaError_t launch_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp,
+                        uint32_t* total, cudaStream_t s, int* launches);
+cudaError_t launch_pool_scatter(const uint32_t* flags, const uint32_t* pos, int64_t n_pos,
+                                int per, int L, uint32_t* pool_xy, cudaStream_t s);
+cudaError_t launch_gather(const uint8_t* img, int N, int B, int L, int per,
+                          const uint32_t* pool_xy, int64_t dn, int64_t cols_pad, int K,
+                          const StepParams& sp, __half* D, float* cf, ColExact* ci,
+                          unsigned long long* vd_max, cudaStream_t s);
+cudaError_t launch_range_prep(const uint8_t* img, int N, int B, const uint32_t* act, int R,
+                              int64_t rows_pad, int K, const StepParams& sp,
+                              const unsigned long long* vd_max, __half* A, RowConst* rc,
+                              cudaStream_t s);
+cudaError_t launch_split_decide(const Best* part, int n_chunks, const RowConst* rc, int R,
+                                int n, int q, int e16, int last, int dn, Best* best,
+                                uint32_t* split, cudaStream_t s);
+cudaError_t launch_split_scatter(const uint32_t* act, const Best* best, const uint32_t* split,
+                                 const uint32_t* split_pos, const RowConst* rc, int R, int B,
+                                 int level, const uint32_t* pool_xy, int per, int L, int dn,
+                                 uint32_t* next_act, void* codes, int64_t code_base,
+                                 cudaStream_t s);
+cudaError_t launch_order_mark(const void* codes, int64_t n_codes, int N, int B_max, int B_min,
+                              uint32_t* cellmap, uint32_t* cellflag, cudaStream_t s);
+cudaError_t launch_order_gather(const void* codes, const uint32_t* cellmap,
+                                const uint32_t* cellflag, const uint32_t* rank, int64_t n_cells,
+                                void* out, cudaStream_t s);
+
+// S sets by quadtree step for the decoder (S = p[level][s] / q[level]).
+struct DecodeS {
+    int B_max;
+    int q[4];
+    int p[4][16];
+};
+cudaError_t launch_decode_pass(const void* codes, int64_t n_codes, const DecodeS& ds,
+                               const uint8_t* src, uint8_t* dst, int N, unsigned* changed,
+                               cudaStream_t s);
+
+}  // namespace fic

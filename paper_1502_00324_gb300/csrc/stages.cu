@@ -1,0 +1,669 @@
+// stages.cu -- the step kernels around the contraction: domain entropy and
+// pool compaction, operand gathers, quadtree split/requeue, record ordering
+// and the decoder pass.
+#include <cfloat>
+
+#include "common.cuh"
+#include "fic.h"
+#include "kernels.h"
+
+namespace fic {
+
+// ---------------------------------------------------------------------------
+// Isometry index maps (Sec. 2: rotations by 90 degrees clockwise, and each
+// rotation mirrored).  T_k = mirror^b o rot^m with m = k & 3, b = k >= 4;
+// rot(x)[i][j] = x[B-1-j][i], mirror(x)[i][j] = x[i][B-1-j].
+// ---------------------------------------------------------------------------
+
+// Source of T_k(x)[i][j] in x.
+__device__ __forceinline__ void iso_fwd_src(int i, int j, int k, int B, int& si, int& sj)
+{
+    if (k >= 4) j = B - 1 - j;
+    for (int m = 0; m < (k & 3); ++m) {
+        const int t = i;
+        i = B - 1 - j;
+        j = t;
+    }
+    si = i;
+    sj = j;
+}
+
+// Source of T_k^-1(x)[i][j] in x; T_k^-1 = rot^-m o mirror^b and
+// rot^-1(x)[i][j] = x[j][B-1-i].
+__device__ __forceinline__ void iso_inv_src(int i, int j, int k, int B, int& si, int& sj)
+{
+    for (int m = 0; m < (k & 3); ++m) {
+        const int t = i;
+        i = j;
+        j = B - 1 - t;
+    }
+    if (k >= 4) j = B - 1 - j;
+    si = i;
+    sj = j;
+}
+
+__device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }
+
+// ---------------------------------------------------------------------------
+// Eq. 5-6 entropy, in bits, from integer counts:
+//   H = log2(P) - (1/P) sum_g q_g log2 q_g,  P = 4n pixels of the 2B x 2B block.
+// The per-count terms q log2 q come from a table built with CUDA's log2.
+// ---------------------------------------------------------------------------
+__global__ void entropy_table_kernel(double* T, int count)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < count) T[q] = q == 0 ? 0.0 : (double)q * log2((double)q);
+}
+
+// One warp per domain position: a 256-bin histogram in shared memory, then
+// the table sum over bins (lane l takes bins 8l..8l+7 in order; the lane
+// partials are combined by a fixed butterfly and lane 0's value is used).
+__global__ void __launch_bounds__(256)
+entropy_kernel(const uint8_t* __restrict__ img, int N, int B, int L, int per, double thr,
+               const double* __restrict__ T, uint32_t* __restrict__ flags,
+               double* __restrict__ Hout, unsigned long long* __restrict__ near)
+{
+    __shared__ unsigned hist[8][256];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t pos = (int64_t)blockIdx.x * 8 + w;
+    const int64_t npos = (int64_t)per * per;
+    if (pos >= npos) return;  // whole warp leaves together
+    const int x = (int)(pos % per) * L, y = (int)(pos / per) * L;
+    const int S = 2 * B, P = S * S;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) hist[w][lane * 8 + b] = 0;
+    __syncwarp();
+    for (int t = lane; t < P; t += 32) {
+        const int yy = y + t / S, xx = x + t % S;
+        atomicAdd(&hist[w][img[(int64_t)yy * N + xx]], 1u);
+    }
+    __syncwarp();
+    double part = 0.0;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) part += T[hist[w][lane * 8 + b]];
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) part += __shfl_xor_sync(0xffffffffu, part, m);
+    if (lane == 0) {
+        const double H = (double)ilog2(P) - part / (double)P;
+        flags[pos] = H > thr ? 1u : 0u;
+        if (Hout) Hout[pos] = H;
+        if (fabs(H - thr) < 1e-9) atomicAdd(near, 1ull);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Device-wide exclusive scan of uint32 (pool compaction, split requeue,
+// record ordering).  Tiles of 4096 elements: per-tile sums, one-block scan
+// of the tile sums, then a per-tile scan with the tile offset.
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total)
+{
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t wtot;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t o = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += o;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t s = lane < nw ? wsum[lane] : 0u;
+        uint32_t si = s;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t o = __shfl_up_sync(0xffffffffu, si, d);
+            if (lane >= d) si += o;
+        }
+        if (lane < nw) wsum[lane] = si - s;
+        if (lane == 31) wtot = si;  // lanes >= nw add 0: lane 31 holds the total
+    }
+    __syncthreads();
+    const uint32_t res = wsum[w] + inc - v;
+    if (total) *total = wtot;
+    __syncthreads();
+    return res;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+scan_reduce_kernel(const uint32_t* __restrict__ in, int64_t n, uint32_t* __restrict__ sums)
+{
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    uint32_t s = 0;
+    for (int i = threadIdx.x; i < kScanTile; i += kScanThreads) {
+        const int64_t g = base + i;
+        if (g < n) s += in[g];
+    }
+    uint32_t tot;
+    block_excl_scan(s, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024)
+scan_top_kernel(uint32_t* __restrict__ sums, int nb, uint32_t* __restrict__ total)
+{
+    // 1024 threads x 4 consecutive items -> up to 4096 tiles
+    uint32_t v[4];
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int g = threadIdx.x * 4 + i;
+        v[i] = g < nb ? sums[g] : 0u;
+        s += v[i];
+    }
+    uint32_t tot;
+    uint32_t off = block_excl_scan(s, &tot);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int g = threadIdx.x * 4 + i;
+        if (g < nb) sums[g] = off;
+        off += v[i];
+    }
+    if (threadIdx.x == 0) *total = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+scan_apply_kernel(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int64_t n,
+                  const uint32_t* __restrict__ sums)
+{
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t g = base + i;
+        v[i] = g < n ? in[g] : 0u;
+        s += v[i];
+    }
+    uint32_t off = block_excl_scan(s, nullptr) + sums[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t g = base + i;
+        if (g < n) out[g] = off;
+        off += v[i];
+    }
+}
+
+int64_t scan_tmp_words(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
+
+cudaError_t launch_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp,
+                        uint32_t* total, cudaStream_t s, int* launches)
+{
+    if (n <= 0) return cudaMemsetAsync(total, 0, sizeof(uint32_t), s);
+    const int64_t nb = (n + kScanTile - 1) / kScanTile;
+    if (nb > 4096) return cudaErrorInvalidValue;
+    scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, tmp);
+    scan_top_kernel<<<1, 1024, 0, s>>>(tmp, (int)nb, total);
+    scan_apply_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, tmp);
+    if (launches) *launches += 3;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Pool list (Sec. 3.3: domain coordinates kept in a list; the list index is
+// the address): admitted positions in raster order, packed x | y << 16.
+// ---------------------------------------------------------------------------
+__global__ void pool_scatter_kernel(const uint32_t* __restrict__ flags,
+                                    const uint32_t* __restrict__ pos, int64_t n_pos, int per,
+                                    int L, uint32_t* __restrict__ pool_xy)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_pos || !flags[i]) return;
+    const uint32_t x = (uint32_t)((i % per) * L), y = (uint32_t)((i / per) * L);
+    pool_xy[pos[i]] = x | (y << 16);
+}
+
+cudaError_t launch_entropy_table(double* T, int count, cudaStream_t s)
+{
+    entropy_table_kernel<<<(count + 255) / 256, 256, 0, s>>>(T, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_entropy(const uint8_t* img, int N, int B, int L, int per, double thr,
+                           const double* T, uint32_t* flags, double* H,
+                           unsigned long long* near, cudaStream_t s)
+{
+    const int64_t npos = (int64_t)per * per;
+    if (npos == 0) return cudaSuccess;
+    entropy_kernel<<<(unsigned)((npos + 7) / 8), 256, 0, s>>>(img, N, B, L, per, thr, T, flags,
+                                                                H, near);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pool_scatter(const uint32_t* flags, const uint32_t* pos, int64_t n_pos,
+                                int per, int L, uint32_t* pool_xy, cudaStream_t s)
+{
+    if (n_pos == 0) return cudaSuccess;
+    pool_scatter_kernel<<<(unsigned)((n_pos + 255) / 256), 256, 0, s>>>(flags, pos, n_pos, per,
+                                                                        L, pool_xy);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Domain gather (Sec. 2 decimation): for pool column c, the B x B array of
+// 2x2 sums d' is written centred (d' - 510, FP16, exact) into the tile
+// layout, with sum d', sum d'^2 and the filter constants m_c, beta_s.
+// K/8 threads per column, each producing one 16-byte row of a core matrix.
+// ---------------------------------------------------------------------------
+template <int K>
+__global__ void __launch_bounds__(256)
+gather_kernel(const uint8_t* __restrict__ img, int N, int B, int L, int per,
+              const uint32_t* __restrict__ pool_xy, int64_t dn, int64_t cols_pad,
+              StepParams sp, __half* __restrict__ D, float* __restrict__ cf,
+              ColExact* __restrict__ ci, unsigned long long* __restrict__ vd_max)
+{
+    constexpr int G = K / 8;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t c = gid / G;
+    const int kg = (int)(gid % G);
+    if (c >= cols_pad) return;  // cols_pad * G is a multiple of 256: whole warps
+    const bool real = c < dn;
+    int x = 0, y = 0;
+    if (real) {
+        if (pool_xy) {
+            const uint32_t v = pool_xy[c];
+            x = (int)(v & 0xffffu);
+            y = (int)(v >> 16);
+        } else {
+            x = (int)(c % per) * L;
+            y = (int)(c / per) * L;
+        }
+    }
+    const int n = B * B;
+    int s = 0, s2 = 0;
+    __align__(16) __half hv[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int k = kg * 8 + e;
+        int val = 0;
+        if (real && k < n) {
+            const int i = k / B, j = k % B;
+            const uint8_t* p0 = img + (int64_t)(y + 2 * i) * N + x + 2 * j;
+            const int d = (int)p0[0] + p0[1] + p0[N] + p0[N + 1];
+            s += d;
+            s2 += d * d;
+            val = d - kDomainCentre;
+        }
+        hv[e] = __int2half_rn(val);
+    }
+    *reinterpret_cast<uint4*>(D + tile_off(c, kg * 8, cols_pad, K)) =
+        *reinterpret_cast<const uint4*>(hv);
+#pragma unroll
+    for (int m = 1; m < G; m <<= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, m);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, m);
+    }
+    if (kg != 0) return;
+    float* col = cf + c * sp.cw;
+    if (real) {
+        const long long vd = (long long)n * s2 - (long long)s * s;
+        col[0] = (float)(s - kDomainCentre * n) * (1.0f / (float)n);
+        for (int t = 0; t < sp.ns; ++t)
+            col[1 + t] = __double2float_rn((double)sp.p[t] * sp.p[t] * (double)vd / (double)n);
+        ci[c] = ColExact{s, s2};
+        atomicMax(vd_max, (unsigned long long)vd);
+    } else {
+        col[0] = 0.0f;
+        for (int t = 0; t < sp.ns; ++t) col[1 + t] = __int_as_float(0x7f800000);
+        ci[c] = ColExact{0, 0};
+    }
+    for (int t = 1 + sp.ns; t < sp.cw; ++t) col[t] = 0.0f;
+}
+
+cudaError_t launch_gather(const uint8_t* img, int N, int B, int L, int per,
+                          const uint32_t* pool_xy, int64_t dn, int64_t cols_pad, int K,
+                          const StepParams& sp, __half* D, float* cf, ColExact* ci,
+                          unsigned long long* vd_max, cudaStream_t s)
+{
+    const int64_t threads = cols_pad * (K / 8);
+    const unsigned blocks = (unsigned)((threads + 255) / 256);
+    switch (K) {
+        case 16:
+            gather_kernel<16><<<blocks, 256, 0, s>>>(img, N, B, L, per, pool_xy, dn, cols_pad,
+                                                     sp, D, cf, ci, vd_max);
+            break;
+        case 64:
+            gather_kernel<64><<<blocks, 256, 0, s>>>(img, N, B, L, per, pool_xy, dn, cols_pad,
+                                                     sp, D, cf, ci, vd_max);
+            break;
+        case 256:
+            gather_kernel<256><<<blocks, 256, 0, s>>>(img, N, B, L, per, pool_xy, dn, cols_pad,
+                                                      sp, D, cf, ci, vd_max);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Range prep: for active range rho and isometry k, row 8 rho + k holds
+// T_k^-1(r) - 128 (so that sum r . T_k(d') = sum T_k^-1(r) . d'); plus the
+// isometry-invariant sums and the filter error bound.  One warp per range.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+range_prep_kernel(const uint8_t* __restrict__ img, int N, int B, const uint32_t* __restrict__ act,
+                  int R, int Rpad, int64_t rows_pad, int K, StepParams sp,
+                  const unsigned long long* __restrict__ vd_max, __half* __restrict__ A,
+                  RowConst* __restrict__ rc)
+{
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rho = blockIdx.x * 8 + w;
+    if (rho >= Rpad) return;
+    const int n = B * B, G = K / 8;
+    const bool real = rho < R;
+    int rx = 0, ry = 0;
+    if (real) {
+        const uint32_t v = act[rho];
+        rx = (int)(v & 0xffffu);
+        ry = (int)(v >> 16);
+    }
+    int sr = 0, sr2 = 0;
+    if (real)
+        for (int t = lane; t < n; t += 32) {
+            const int v = img[(int64_t)(ry + t / B) * N + rx + t % B];
+            sr += v;
+            sr2 += v * v;
+        }
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, m);
+        sr2 += __shfl_xor_sync(0xffffffffu, sr2, m);
+    }
+    for (int v = lane; v < 8 * G; v += 32) {
+        const int k = v / G, kg = v % G;
+        __align__(16) __half hv[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int kk = kg * 8 + e;
+            int val = 0;
+            if (real && kk < n) {
+                int si, sj;
+                iso_inv_src(kk / B, kk % B, k, B, si, sj);
+                val = (int)img[(int64_t)(ry + si) * N + rx + sj] - kRangeCentre;
+            }
+            hv[e] = __int2half_rn(val);
+        }
+        *reinterpret_cast<uint4*>(A + tile_off((int64_t)rho * 8 + k, kg * 8, rows_pad, K)) =
+            *reinterpret_cast<const uint4*>(hv);
+    }
+    if (lane == 0) {
+        RowConst r{0, 0, 0.0f, 0.0f};
+        if (real) {
+            const double u = 0x1p-24;
+            const double vr = (double)((long long)n * sr2 - (long long)sr * sr);
+            const double vdm = (double)(*vd_max);
+            int pm = 0;
+            for (int t = 0; t < sp.ns; ++t) pm = max(pm, sp.p[t]);
+            const double bound = (2.0 * u + u * u) *
+                                 (8.0 * pm * sp.q * sqrt(vr * vdm) + (double)pm * pm * vdm) /
+                                 (double)n;
+            r.sr = sr;
+            r.sr2 = sr2;
+            r.a = (float)(sr - kRangeCentre * n);
+            r.delta = __double2float_ru(2.0 * bound);
+        }
+        rc[rho] = r;
+    }
+}
+
+cudaError_t launch_range_prep(const uint8_t* img, int N, int B, const uint32_t* act, int R,
+                              int64_t rows_pad, int K, const StepParams& sp,
+                              const unsigned long long* vd_max, __half* A, RowConst* rc,
+                              cudaStream_t s)
+{
+    const int Rpad = (int)(rows_pad / 8);
+    if (Rpad == 0) return cudaSuccess;
+    range_prep_kernel<<<(Rpad + 7) / 8, 256, 0, s>>>(img, N, B, act, R, Rpad, rows_pad, K, sp,
+                                                     vd_max, A, rc);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Split / requeue (Sec. 2): reduce the per-chunk partial bests, then split
+// iff the step is not the last and the RMS error exceeds the tolerance,
+//   sqrt(E/n) > e16/16  <=>  256 score > 16 q^2 n^2 e16^2,
+// score = 16 q^2 Vr + h.  The last step always stores its best mapping.
+// ---------------------------------------------------------------------------
+__global__ void split_decide_kernel(const Best* __restrict__ part, int n_chunks,
+                                    const RowConst* __restrict__ rc, int R, int n, int q,
+                                    int e16, int last, int dn, Best* __restrict__ best,
+                                    uint32_t* __restrict__ split)
+{
+    const int rho = blockIdx.x * blockDim.x + threadIdx.x;
+    if (rho >= R) return;
+    long long h = kNoCandidate;
+    unsigned idx = 0xffffffffu;
+    for (int c = 0; c < n_chunks; ++c) {
+        const Best b = part[(int64_t)rho * n_chunks + c];
+        if (key_less(b.h, b.idx, h, idx)) {
+            h = b.h;
+            idx = b.idx;
+        }
+    }
+    bool sp;
+    if (dn == 0 || h == kNoCandidate) {
+        sp = !last;
+    } else {
+        const RowConst r = rc[rho];
+        const long long vr = (long long)n * r.sr2 - (long long)r.sr * r.sr;
+        const long long qq = (long long)q * q;
+        const long long score = 16LL * qq * vr + h;
+        const long long lim = 16LL * qq * n * n * (long long)e16 * e16;
+        sp = !last && 256LL * score > lim;
+    }
+    Best b;
+    b.h = h;
+    b.idx = idx;
+    b.pad = 0;
+    best[rho] = b;
+    split[rho] = sp ? 1u : 0u;
+}
+
+__global__ void split_scatter_kernel(const uint32_t* __restrict__ act, const Best* __restrict__ best,
+                                     const uint32_t* __restrict__ split,
+                                     const uint32_t* __restrict__ split_pos,
+                                     const RowConst* __restrict__ rc, int R, int B, int level,
+                                     const uint32_t* __restrict__ pool_xy, int per, int L, int dn,
+                                     uint32_t* __restrict__ next_act, fic_code* __restrict__ codes,
+                                     int64_t code_base)
+{
+    const int rho = blockIdx.x * blockDim.x + threadIdx.x;
+    if (rho >= R) return;
+    const uint32_t v = act[rho];
+    const uint32_t x = v & 0xffffu, y = v >> 16;
+    if (split[rho]) {
+        const uint32_t hb = (uint32_t)B / 2;
+        uint32_t* o = next_act + 4 * (int64_t)split_pos[rho];
+        o[0] = x | (y << 16);
+        o[1] = (x + hb) | (y << 16);
+        o[2] = x | ((y + hb) << 16);
+        o[3] = (x + hb) | ((y + hb) << 16);
+        return;
+    }
+    const int n = B * B;
+    const Best b = best[rho];
+    fic_code c;
+    c.rx = (uint16_t)x;
+    c.ry = (uint16_t)y;
+    c.level = (uint8_t)level;
+    const int oq = rc[rho].sr / (2 * n);
+    c.o_q = (uint8_t)(oq > 127 ? 127 : oq);
+    if (dn == 0 || b.h == kNoCandidate) {
+        c.iso = 0;
+        c.s_idx = 0xff;
+        c.dx = 0;
+        c.dy = 0;
+        c.pool_idx = 0xffffffffu;
+    } else {
+        const uint32_t col = b.idx >> 7;
+        c.iso = (uint8_t)((b.idx >> 4) & 7);
+        c.s_idx = (uint8_t)(b.idx & 15);
+        c.pool_idx = col;
+        if (pool_xy) {
+            const uint32_t pv = pool_xy[col];
+            c.dx = (uint16_t)(pv & 0xffffu);
+            c.dy = (uint16_t)(pv >> 16);
+        } else {
+            c.dx = (uint16_t)((col % (uint32_t)per) * L);
+            c.dy = (uint16_t)((col / (uint32_t)per) * L);
+        }
+    }
+    codes[code_base + rho - (int64_t)split_pos[rho]] = c;
+}
+
+cudaError_t launch_split_decide(const Best* part, int n_chunks, const RowConst* rc, int R,
+                                int n, int q, int e16, int last, int dn, Best* best,
+                                uint32_t* split, cudaStream_t s)
+{
+    if (R == 0) return cudaSuccess;
+    split_decide_kernel<<<(R + 255) / 256, 256, 0, s>>>(part, n_chunks, rc, R, n, q, e16, last,
+                                                        dn, best, split);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_scatter(const uint32_t* act, const Best* best, const uint32_t* split,
+                                 const uint32_t* split_pos, const RowConst* rc, int R, int B,
+                                 int level, const uint32_t* pool_xy, int per, int L, int dn,
+                                 uint32_t* next_act, void* codes, int64_t code_base,
+                                 cudaStream_t s)
+{
+    if (R == 0) return cudaSuccess;
+    split_scatter_kernel<<<(R + 255) / 256, 256, 0, s>>>(
+        act, best, split, split_pos, rc, R, B, level, pool_xy, per, L, dn, next_act,
+        static_cast<fic_code*>(codes), code_base);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Record order (Sec. 3.3): top-level ranges in raster order, then the
+// quadtree depth first in TL, TR, BL, BR order.  Leaves tile the image, so
+// that order is the order of their top-left finest cells under the key
+// (top-level raster index, Morton code with the row bit above the column bit).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t spread_bits(uint32_t v)
+{
+    v &= 0xffffu;
+    v = (v | (v << 8)) & 0x00ff00ffu;
+    v = (v | (v << 4)) & 0x0f0f0f0fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+
+__global__ void order_mark_kernel(const fic_code* __restrict__ codes, int64_t n_codes, int N,
+                                  int B_max, int B_min, uint32_t* __restrict__ cellmap,
+                                  uint32_t* __restrict__ cellflag)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_codes) return;
+    const fic_code c = codes[i];
+    const int cpt = B_max / B_min;  // finest cells per top-level side
+    const int cx = c.rx / B_min, cy = c.ry / B_min;
+    const int tops = N / B_max;
+    const int64_t top = (int64_t)(cy / cpt) * tops + cx / cpt;
+    const uint32_t morton = (spread_bits((uint32_t)(cy % cpt)) << 1) | spread_bits((uint32_t)(cx % cpt));
+    const int64_t z = top * cpt * cpt + morton;
+    cellmap[z] = (uint32_t)i;
+    cellflag[z] = 1u;
+}
+
+__global__ void order_gather_kernel(const fic_code* __restrict__ codes,
+                                    const uint32_t* __restrict__ cellmap,
+                                    const uint32_t* __restrict__ cellflag,
+                                    const uint32_t* __restrict__ rank, int64_t n_cells,
+                                    fic_code* __restrict__ out)
+{
+    const int64_t z = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= n_cells || !cellflag[z]) return;
+    out[rank[z]] = codes[cellmap[z]];
+}
+
+cudaError_t launch_order_mark(const void* codes, int64_t n_codes, int N, int B_max, int B_min,
+                              uint32_t* cellmap, uint32_t* cellflag, cudaStream_t s)
+{
+    if (n_codes == 0) return cudaSuccess;
+    order_mark_kernel<<<(unsigned)((n_codes + 255) / 256), 256, 0, s>>>(
+        static_cast<const fic_code*>(codes), n_codes, N, B_max, B_min, cellmap, cellflag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_order_gather(const void* codes, const uint32_t* cellmap,
+                                const uint32_t* cellflag, const uint32_t* rank, int64_t n_cells,
+                                void* out, cudaStream_t s)
+{
+    if (n_cells == 0) return cudaSuccess;
+    order_gather_kernel<<<(unsigned)((n_cells + 255) / 256), 256, 0, s>>>(
+        static_cast<const fic_code*>(codes), cellmap, cellflag, rank, n_cells,
+        static_cast<fic_code*>(out));
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Decoder pass (Sec. 2: each range rebuilt from its domain and mapping):
+//   pixel = clamp(floor(((2 o_q + 1) 4qn + p (n T(d')_ij - sum d') + 2qn) / (4qn)), 0, 255)
+// i.e. (2 o_q + 1) + S (d - mean d) with d = T(d')/4, rounded half up.
+// One warp per record; *changed is set when any pixel differs from src.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+decode_pass_kernel(const fic_code* __restrict__ codes, int64_t n_codes, DecodeS ds,
+                   const uint8_t* __restrict__ src, uint8_t* __restrict__ dst, int N,
+                   unsigned* __restrict__ changed)
+{
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t ci = (int64_t)blockIdx.x * 8 + w;
+    if (ci >= n_codes) return;
+    const fic_code c = codes[ci];
+    const int B = ds.B_max >> c.level, n = B * B;
+    bool diff = false;
+    if (c.s_idx == 0xff) {
+        for (int t = lane; t < n; t += 32) {
+            const int64_t o = (int64_t)(c.ry + t / B) * N + c.rx + t % B;
+            const uint8_t v = (uint8_t)(2 * c.o_q + 1);
+            diff |= src[o] != v;
+            dst[o] = v;
+        }
+    } else {
+        // sum d' over the domain (isometry invariant)
+        long long sd = 0;
+        for (int t = lane; t < n; t += 32) {
+            const uint8_t* p0 = src + (int64_t)(c.dy + 2 * (t / B)) * N + c.dx + 2 * (t % B);
+            sd += (int)p0[0] + p0[1] + p0[N] + p0[N + 1];
+        }
+#pragma unroll
+        for (int m = 16; m >= 1; m >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, m);
+        const long long p = ds.p[c.level][c.s_idx], q = ds.q[c.level];
+        const long long den = 4 * q * n;
+        for (int t = lane; t < n; t += 32) {
+            const int i = t / B, j = t % B;
+            int si, sj;
+            iso_fwd_src(i, j, c.iso, B, si, sj);
+            const uint8_t* p0 = src + (int64_t)(c.dy + 2 * si) * N + c.dx + 2 * sj;
+            const long long d = (int)p0[0] + p0[1] + p0[N] + p0[N + 1];
+            const long long num = (2LL * c.o_q + 1) * den + p * ((long long)n * d - sd) + den / 2;
+            long long v = num >= 0 ? num / den : -((-num + den - 1) / den);
+            v = v < 0 ? 0 : (v > 255 ? 255 : v);
+            const int64_t o = (int64_t)(c.ry + i) * N + c.rx + j;
+            diff |= src[o] != (uint8_t)v;
+            dst[o] = (uint8_t)v;
+        }
+    }
+    if (__any_sync(0xffffffffu, diff) && lane == 0) atomicOr(changed, 1u);
+}
+
+cudaError_t launch_decode_pass(const void* codes, int64_t n_codes, const DecodeS& ds,
+                               const uint8_t* src, uint8_t* dst, int N, unsigned* changed,
+                               cudaStream_t s)
+{
+    if (n_codes == 0) return cudaSuccess;
+    decode_pass_kernel<<<(unsigned)((n_codes + 7) / 8), 256, 0, s>>>(
+        static_cast<const fic_code*>(codes), n_codes, ds, src, dst, N, changed);
+    return cudaGetLastError();
+}
+
+}  // namespace fic

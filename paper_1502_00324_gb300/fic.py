@@ -1,0 +1,266 @@
+"""Thin ctypes binding of libfic.so (include/fic.h).
+
+Argument marshalling only: every step of the search runs in the library's
+CUDA kernels.  If the library is missing the import of a function raises;
+there is no fallback path.  PyTorch is used only to hand over device memory
+and streams (``data_ptr()``, ``torch.cuda.current_stream().cuda_stream``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfic.so")
+
+FIC_OK = 0
+FIC_EINVAL = -1
+FIC_ENOMEM = -2
+FIC_ECUDA = -3
+FIC_ETIMEOUT = -4
+FIC_EBUSY = -5
+FIC_ENODEV = -6
+FIC_ECAP = -7
+FIC_ENOTREADY = -8
+MAX_LEVELS = 4
+MAX_S = 16
+ENGINE_TENSOR = 0
+ENGINE_PLAIN = 1
+KERNEL_KINDS = ["entropy", "scan", "gather", "range_prep", "contract_tc", "contract_plain",
+                "split", "order", "decode", "misc"]
+
+
+class FicSset(C.Structure):
+    _fields_ = [("n_s", C.c_int32), ("q", C.c_int32), ("p", C.c_int32 * MAX_S)]
+
+
+class FicCode(C.Structure):
+    _fields_ = [("rx", C.c_uint16), ("ry", C.c_uint16), ("dx", C.c_uint16), ("dy", C.c_uint16),
+                ("pool_idx", C.c_uint32), ("level", C.c_uint8), ("iso", C.c_uint8),
+                ("s_idx", C.c_uint8), ("o_q", C.c_uint8)]
+
+
+class FicResult(C.Structure):
+    _fields_ = [("codes", C.POINTER(FicCode)), ("n_codes", C.c_int64), ("n_levels", C.c_int32),
+                ("N", C.c_int32), ("B_max", C.c_int32), ("owns_codes", C.c_int32),
+                ("S_sets", FicSset * MAX_LEVELS), ("n_positions", C.c_int64 * MAX_LEVELS),
+                ("pool_size", C.c_int64 * MAX_LEVELS), ("ranges", C.c_int64 * MAX_LEVELS),
+                ("matches", C.c_int64 * MAX_LEVELS), ("near_thresh", C.c_int64 * MAX_LEVELS)]
+
+
+class FicParams(C.Structure):
+    _fields_ = [("N", C.c_int32), ("B_max", C.c_int32), ("B_min", C.c_int32), ("L", C.c_int32),
+                ("entropy_thresh", C.c_double), ("err_tol", C.c_double),
+                ("S_sets", FicSset * MAX_LEVELS), ("engine", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class FicStats(C.Structure):
+    _fields_ = [("launches", C.c_int64 * 10), ("ms", C.c_double * 10),
+                ("flops", C.c_double * 10), ("bytes", C.c_double * 10), ("matches", C.c_int64)]
+
+
+CODE_DTYPE = np.dtype([("rx", np.uint16), ("ry", np.uint16), ("dx", np.uint16),
+                       ("dy", np.uint16), ("pool_idx", np.uint32), ("level", np.uint8),
+                       ("iso", np.uint8), ("s_idx", np.uint8), ("o_q", np.uint8)])
+assert CODE_DTYPE.itemsize == C.sizeof(FicCode) == 16
+
+EXPORTS = ["fic_encode", "fic_encode_ex", "fic_decode", "fic_domain_pool", "fic_result_free",
+           "fic_strerror", "fic_stats_reset", "fic_stats_read", "fic_version"]
+
+
+class FicError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__(f"{what}: {strerror(status)} ({status})")
+
+
+_lib = None
+
+
+def lib():
+    """Load libfic.so (built by paper_1502_00324_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libfic.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = C.CDLL(LIB_PATH)
+    vp = C.c_void_p
+    L.fic_encode.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
+                             C.POINTER(FicSset), C.c_double, C.POINTER(FicResult), vp]
+    L.fic_encode_ex.argtypes = [vp, C.POINTER(FicParams), vp, C.c_int64, C.POINTER(FicResult), vp]
+    L.fic_decode.argtypes = [C.POINTER(FicResult), C.c_int, C.c_int, vp, C.POINTER(C.c_int), vp]
+    L.fic_domain_pool.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_double,
+                                  C.POINTER(C.c_int32), C.c_int64, C.POINTER(C.c_int64),
+                                  C.POINTER(C.c_double), C.POINTER(C.c_int64), vp]
+    L.fic_result_free.argtypes = [C.POINTER(FicResult)]
+    L.fic_result_free.restype = None
+    L.fic_strerror.argtypes = [C.c_int]
+    L.fic_strerror.restype = C.c_char_p
+    L.fic_stats_reset.argtypes = [C.c_int]
+    L.fic_stats_read.argtypes = [C.POINTER(FicStats)]
+    L.fic_version.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def strerror(status: int) -> str:
+    return lib().fic_strerror(status).decode()
+
+
+def _check(st, what):
+    if st != FIC_OK:
+        raise FicError(st, what)
+
+
+def _ptr(x):
+    """(address, keepalive) of a numpy array or torch tensor."""
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data, x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr(), x
+    raise TypeError(f"expected numpy array or torch tensor, got {type(x)}")
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+def make_ssets(ssets):
+    """[(q, [p...]), ...] (one per quadtree step) -> FicSset array."""
+    arr = (FicSset * MAX_LEVELS)()
+    for i, (q, ps) in enumerate(ssets):
+        arr[i].n_s = len(ps)
+        arr[i].q = q
+        for j, p in enumerate(ps):
+            arr[i].p[j] = p
+    return arr
+
+
+class Encoded:
+    """Result of an encode: codes (numpy structured array on the host, or the
+    caller's device buffer) plus per-step counters."""
+
+    def __init__(self, res: FicResult, codes):
+        self._res = res
+        self.codes = codes
+        nl = res.n_levels
+        self.N = res.N
+        self.n_codes = int(res.n_codes)
+        self.n_levels = nl
+        self.n_positions = [int(res.n_positions[i]) for i in range(nl)]
+        self.pool_size = [int(res.pool_size[i]) for i in range(nl)]
+        self.ranges = [int(res.ranges[i]) for i in range(nl)]
+        self.matches = [int(res.matches[i]) for i in range(nl)]
+        self.near_thresh = [int(res.near_thresh[i]) for i in range(nl)]
+
+    @property
+    def total_matches(self):
+        return sum(self.matches)
+
+
+def fic_encode_ex(img, N, B_max, B_min, L, entropy_thresh, ssets, err_tol,
+                  engine=ENGINE_TENSOR, stream=None, codes_out=None):
+    """Encode one N x N uint8 image (numpy array, or torch tensor on the host
+    or the GPU).  ``codes_out``: optional torch/numpy buffer of 16-byte
+    records receiving the codes (host or device); otherwise a host array is
+    returned."""
+    p = FicParams()
+    p.N, p.B_max, p.B_min, p.L = N, B_max, B_min, L
+    p.entropy_thresh = float(entropy_thresh)
+    p.err_tol = float(err_tol)
+    p.S_sets = make_ssets(ssets)
+    p.engine = engine
+    p.reserved = 0
+    ip, keep = _ptr(img)
+    res = FicResult()
+    if codes_out is not None:
+        cp, keep2 = _ptr(codes_out)
+        cap = (codes_out.nbytes if isinstance(codes_out, np.ndarray)
+               else codes_out.numel() * codes_out.element_size()) // 16
+        st = lib().fic_encode_ex(ip, C.byref(p), cp, cap, C.byref(res), _stream(stream))
+        _check(st, "fic_encode_ex")
+        return Encoded(res, codes_out)
+    st = lib().fic_encode_ex(ip, C.byref(p), None, 0, C.byref(res), _stream(stream))
+    _check(st, "fic_encode_ex")
+    return _adopt(res)
+
+
+def _adopt(res: FicResult) -> Encoded:
+    """Copy library-owned host codes into numpy and free the library array;
+    the result then points at the numpy copy (for fic_decode)."""
+    n = int(res.n_codes)
+    codes = np.empty(n, CODE_DTYPE)
+    if n:
+        C.memmove(codes.ctypes.data, res.codes, n * 16)
+    lib().fic_result_free(C.byref(res))
+    res.codes = C.cast(C.c_void_p(codes.ctypes.data), C.POINTER(FicCode))
+    res.owns_codes = 0
+    res.n_codes = n
+    out = Encoded(res, codes)
+    out._keep = codes
+    return out
+
+
+def fic_encode(img, N, B_max, B_min, L, entropy_thresh, ssets, err_tol, stream=None):
+    """fic_encode of include/fic.h (tensor-core engine, host codes)."""
+    ip, keep = _ptr(img)
+    res = FicResult()
+    ss = make_ssets(ssets)
+    st = lib().fic_encode(ip, N, B_max, B_min, L, float(entropy_thresh), ss, float(err_tol),
+                          C.byref(res), _stream(stream))
+    _check(st, "fic_encode")
+    return _adopt(res)
+
+
+def fic_decode(enc: Encoded, iters_max=64, out=None, stream=None):
+    """GPU decode of an Encoded result; returns (image, passes used)."""
+    N = enc.N
+    if out is None:
+        out = np.empty((N, N), np.uint8)
+    op, keep = _ptr(out)
+    used = C.c_int(0)
+    st = lib().fic_decode(C.byref(enc._res), N, iters_max, op, C.byref(used), _stream(stream))
+    _check(st, "fic_decode")
+    return out, int(used.value)
+
+
+def fic_domain_pool(img, N, B, L, entropy_thresh, stream=None):
+    """Kernels (a)+(b) alone: (pool positions (DN, 2), entropy per position,
+    near-threshold count)."""
+    ip, keep = _ptr(img)
+    per = (N - 2 * B) // L + 1 if N >= 2 * B else 0
+    npos = per * per
+    ent = np.empty(max(npos, 1), np.float64)
+    xy = np.empty((max(npos, 1), 2), np.int32)
+    dn = C.c_int64(0)
+    near = C.c_int64(0)
+    st = lib().fic_domain_pool(ip, N, B, L, float(entropy_thresh),
+                               xy.ctypes.data_as(C.POINTER(C.c_int32)), npos, C.byref(dn),
+                               ent.ctypes.data_as(C.POINTER(C.c_double)), C.byref(near),
+                               _stream(stream))
+    _check(st, "fic_domain_pool")
+    return xy[: dn.value].copy(), ent[:npos].copy(), int(near.value)
+
+
+def fic_stats_reset(timing=False):
+    _check(lib().fic_stats_reset(1 if timing else 0), "fic_stats_reset")
+
+
+def fic_stats_read():
+    s = FicStats()
+    _check(lib().fic_stats_read(C.byref(s)), "fic_stats_read")
+    return {k: dict(launches=int(s.launches[i]), ms=float(s.ms[i]), flops=float(s.flops[i]),
+                    bytes=float(s.bytes[i])) for i, k in enumerate(KERNEL_KINDS)} | {
+        "matches": int(s.matches)}
+
+
+def fic_version():
+    return lib().fic_version().decode()

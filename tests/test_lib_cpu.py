@@ -1,0 +1,78 @@
+"""Host-side checks of the C-ABI library that need no GPU: it builds for
+sm_103a, loads, exports every function include/fic.h declares, and rejects
+bad arguments before touching a device."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def fic():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1502_00324_gb300 as pkg
+    return pkg
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "fic.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fic_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_header_function(fic):
+    names = header_functions()
+    assert "fic_encode" in names and "fic_decode" in names
+    lib = fic.lib()
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(fic.fic.EXPORTS) <= set(names)
+
+
+def test_library_targets_sm103a(fic):
+    assert "sm_103a" in fic.fic_version()
+
+
+def test_strerror(fic):
+    for st in range(0, -9, -1):
+        assert fic.fic.strerror(st) not in ("", "unknown status")
+    assert fic.fic.strerror(-99) == "unknown status"
+
+
+@pytest.mark.parametrize("bad", [
+    dict(N=100, B_max=16),          # N % B_max != 0
+    dict(B_max=4, B_min=8),          # B_min > B_max
+    dict(B_max=12),                  # not a power of two
+    dict(B_max=32, N=512),           # side above 16
+    dict(L=0),
+    dict(err_tol=-1.0),
+    dict(err_tol=300.0),
+    dict(ssets=[(10, [11]), (10, [2, 4]), (10, [3, 8])]),   # S > 1
+    dict(ssets=[(0, [1]), (10, [2, 4]), (10, [3, 8])]),     # q < 1
+    dict(ssets=[(10, []), (10, [2, 4]), (10, [3, 8])]),     # empty set
+    dict(engine=7),
+])
+def test_bad_arguments_rejected_on_host(fic, bad):
+    args = dict(N=64, B_max=16, B_min=4, L=1, thr=-1.0, err_tol=8.0,
+                ssets=[(10, [1]), (10, [2, 4]), (10, [3, 8])], engine=0)
+    args.update(bad)
+    img = np.zeros((64, 64), np.uint8)
+    with pytest.raises(fic.FicError) as e:
+        fic.fic_encode_ex(img, args["N"], args["B_max"], args["B_min"], args["L"], args["thr"],
+                          args["ssets"], args["err_tol"], engine=args["engine"])
+    assert e.value.status == fic.fic.FIC_EINVAL
+
+
+def test_struct_layouts(fic):
+    f = fic.fic
+    assert C.sizeof(f.FicCode) == 16
+    assert C.sizeof(f.FicSset) == 72
+    # fic_result / fic_params are plain C layouts of int32/int64/double fields
+    assert C.sizeof(f.FicParams) == 4 * 4 + 2 * 8 + 4 * 72 + 2 * 4
