@@ -175,6 +175,8 @@ def run_gpu(args):
     import torch
     import paper_1502_00324_gb300 as pkg
 
+    legs = set(args.legs.split(","))
+
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -236,27 +238,30 @@ def run_gpu(args):
     clocks = sampler.stop()
     codes_t = dcodes[: r_t.n_codes * 16].cpu().numpy().copy()
 
-    # CUDA-core engine on the same workload (fewer steps; it is ~10x slower)
+    # CUDA-core engine on the same workload (fewer steps; it is much slower)
     psteps = max(1, min(args.steps, 3))
-    ms_p, m_p, st_p, r_p, _ = timed(pkg.ENGINE_PLAIN, psteps, 1, False)
-    codes_p = dcodes[: r_p.n_codes * 16].cpu().numpy().copy()
-    identical = bool(r_t.n_codes == r_p.n_codes and np.array_equal(codes_t, codes_p))
+    ms_p, m_p, identical = float("nan"), 0, None
+    if "plain" in legs:
+        ms_p, m_p, st_p, r_p, _ = timed(pkg.ENGINE_PLAIN, psteps, 1, False)
+        codes_p = dcodes[: r_p.n_codes * 16].cpu().numpy().copy()
+        identical = bool(r_t.n_codes == r_p.n_codes and np.array_equal(codes_t, codes_p))
 
     # end to end through the C ABI with host buffers (H2D image, D2H records)
-    himg = torch.from_numpy(img).pin_memory()
-    hcodes = torch.empty(cap * 16, dtype=torch.uint8).pin_memory()
-    for _ in range(max(1, args.warmup)):
-        enc(pkg.ENGINE_TENSOR, src=himg, out=hcodes)
-    torch.cuda.synchronize()
-    barrier()
-    t0 = time.perf_counter()
-    e2e_m = 0
-    for _ in range(args.steps):
-        r = enc(pkg.ENGINE_TENSOR, src=himg, out=hcodes)
-        e2e_m += r.total_matches
-    torch.cuda.synchronize()
-    barrier()
-    e2e_s = time.perf_counter() - t0
+    e2e_m, e2e_s = 0, float("nan")
+    if "e2e" in legs:
+        himg = torch.from_numpy(img).pin_memory()
+        hcodes = torch.empty(cap * 16, dtype=torch.uint8).pin_memory()
+        for _ in range(max(1, args.warmup)):
+            enc(pkg.ENGINE_TENSOR, src=himg, out=hcodes)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            r = enc(pkg.ENGINE_TENSOR, src=himg, out=hcodes)
+            e2e_m += r.total_matches
+        torch.cuda.synchronize()
+        barrier()
+        e2e_s = time.perf_counter() - t0
 
     # max over ranks of the times; sum of work
     vals = torch.tensor([ms_t, float(m_t), e2e_s, float(e2e_m), ms_p, float(m_p)],
@@ -276,7 +281,7 @@ def run_gpu(args):
         return 0
 
     gmatch_t = m_t / (ms_t / 1e3) / 1e9
-    gmatch_p = m_p / (ms_p / 1e3) / 1e9
+    gmatch_p = m_p / (ms_p / 1e3) / 1e9 if m_p else None
     ms_per_img = ms_t / args.steps
 
     # roofline of the dominant kernel (the fused contraction + scoring)
@@ -292,7 +297,7 @@ def run_gpu(args):
     launches = sum(v["launches"] for k, v in st_t.items() if isinstance(v, dict))
 
     cpu = None
-    if not args.no_cpu_baseline:
+    if "cpu" in legs:
         # oracle rate per step on a bounded sample, weighted by this encode's
         # per-step match counts (the oracle's counts are the same: parity)
         import oracle
@@ -316,8 +321,9 @@ def run_gpu(args):
         "data": "synthetic (seeded 1/f images, stand-ins for the paper's test images)",
         "config": config_dict(w, {"parallelism": f"replicas x{world}"}),
         "ms_per_image": ms_per_img,
-        "plain": {"value": gmatch_p, "unit": "Gmatch/s", "ms_per_image": ms_p / psteps},
-        "tensor_over_plain": gmatch_t / gmatch_p,
+        "plain": {"value": gmatch_p, "unit": "Gmatch/s",
+                  "ms_per_image": (ms_p / psteps) if m_p else None},
+        "tensor_over_plain": (gmatch_t / gmatch_p) if gmatch_p else None,
         "codes_identical_tensor_vs_plain": identical,
         "matches_per_image": r_t.total_matches,
         "per_level": {"ranges": r_t.ranges, "pool": r_t.pool_size, "matches": r_t.matches},
@@ -328,7 +334,7 @@ def run_gpu(args):
                      "peak_note": "measured bf16 dense burst (MEASURED_PEAKS.json); fp16 dense "
                                   "nominal equal"},
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_m / e2e_s / 1e9, "unit": "Gmatch/s",
+        "e2e": {"value": (e2e_m / e2e_s / 1e9) if e2e_m else None, "unit": "Gmatch/s",
                 "h2d_bytes_per_step": int(N * N), "d2h_bytes_per_step": int(r_t.n_codes * 16)},
         "gpu_launches": int(launches),
         "clocks": clocks,
@@ -347,7 +353,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--legs", default="tensor,plain,e2e,cpu",
+                    help="measurements to run (profiling runs use 'tensor' alone)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
