@@ -173,6 +173,30 @@ int fic_domain_pool(const uint8_t* img, int N, int B, int L, double entropy_thre
                     int32_t* pool_xy, int64_t cap, int64_t* dn, double* entropy,
                     int64_t* near, void* stream);
 
+/* fic_domain_pool_noalloc -- fic_domain_pool for callers that cannot
+ * allocate device memory.  The paper has no counterpart: this entry point
+ * exists for deployment.  Some callers must not call cudaMalloc: code that
+ * runs in a host callback, a plugin handed device buffers by its host
+ * application, or a process that reserved all device memory up front.  This
+ * call allocates nothing (no cudaMalloc, cudaFree or allocating library
+ * routine); the caller passes device buffers for the input and the outputs,
+ * and the intermediates live in one static device array of the library
+ * (about 8.1 MB per GPU, held until the process exits).
+ *   d_img      device, N*N bytes, read only.
+ *   d_pool_xy  device, cap uint32 entries: admitted positions in raster
+ *              order, packed x | (y << 16).  May be NULL with cap 0.
+ *   dn, near   host outputs: pool size; positions with |H - thr| < 1e-9.
+ *   d_entropy  device, n_positions doubles (eq. 5-6, bits), or NULL.
+ * Returns FIC_EINVAL when n_positions = ((N-2B)/L+1)^2 exceeds
+ * FIC_NOALLOC_MAX_POSITIONS or a buffer is not device memory, FIC_ECAP
+ * (with *dn set) when cap < DN.  The first call on each device sets the
+ * scratch up (symbol lookup and a table kernel): make it before any stream
+ * capture.  Calls share the scratch: calls that overlap on the GPU race. */
+#define FIC_NOALLOC_MAX_POSITIONS (1 << 20)
+int fic_domain_pool_noalloc(const uint8_t* d_img, int N, int B, int L,
+                            double entropy_thresh, uint32_t* d_pool_xy, int64_t cap,
+                            int64_t* dn, double* d_entropy, int64_t* near, void* stream);
+
 /* Frees the library-owned parts of a result (the code array when
  * owns_codes).  Safe on a zeroed struct. */
 void fic_result_free(fic_result* r);

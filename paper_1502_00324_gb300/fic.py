@@ -68,7 +68,8 @@ CODE_DTYPE = np.dtype([("rx", np.uint16), ("ry", np.uint16), ("dx", np.uint16),
 assert CODE_DTYPE.itemsize == C.sizeof(FicCode) == 16
 
 EXPORTS = ["fic_encode", "fic_encode_ex", "fic_decode", "fic_domain_pool", "fic_result_free",
-           "fic_strerror", "fic_stats_reset", "fic_stats_read", "fic_version"]
+           "fic_strerror", "fic_stats_reset", "fic_stats_read", "fic_version",
+           "fic_domain_pool_noalloc"]
 
 
 class FicError(RuntimeError):
@@ -103,6 +104,9 @@ def lib():
     L.fic_stats_reset.argtypes = [C.c_int]
     L.fic_stats_read.argtypes = [C.POINTER(FicStats)]
     L.fic_version.restype = C.c_char_p
+    L.fic_domain_pool_noalloc.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_double, vp,
+                                          C.c_int64, C.POINTER(C.c_int64), vp,
+                                          C.POINTER(C.c_int64), vp]
     _lib = L
     return L
 
@@ -264,3 +268,21 @@ def fic_stats_read():
 
 def fic_version():
     return lib().fic_version().decode()
+
+
+def fic_domain_pool_noalloc(d_img, N, B, L, entropy_thresh, d_pool_xy, d_entropy=None,
+                            stream=None):
+    """fic_domain_pool for callers that cannot allocate device memory: all
+    buffers are the caller's device tensors (``d_pool_xy``: int32/uint32
+    tensor receiving packed x | y << 16; ``d_entropy``: float64 tensor or
+    None).  Returns (pool size, near-threshold count)."""
+    ip, keep = _ptr(d_img)
+    pp, keep2 = _ptr(d_pool_xy)
+    cap = d_pool_xy.numel()
+    ep = d_entropy.data_ptr() if d_entropy is not None else None
+    dn = C.c_int64(0)
+    near = C.c_int64(0)
+    st = lib().fic_domain_pool_noalloc(ip, N, B, L, float(entropy_thresh), pp, cap, C.byref(dn),
+                                       ep, C.byref(near), _stream(stream))
+    _check(st, "fic_domain_pool_noalloc")
+    return int(dn.value), int(near.value)
