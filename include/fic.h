@@ -239,6 +239,10 @@ int fic_stats_read(fic_stats* out);
 /* Library build string (compiled architectures and version). */
 const char* fic_version(void);
 
+/* Name and text of the last CUDA error behind a FIC_ECUDA / FIC_ENOMEM
+ * returned on this thread ("" if none).  Static per-thread storage. */
+const char* fic_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

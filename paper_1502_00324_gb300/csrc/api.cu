@@ -125,6 +125,7 @@ struct Scalars {
     uint32_t changed;
     unsigned long long near;
     unsigned long long vd_max;
+    unsigned long long vd_min_key;
     int err;
     int pad;
 };
@@ -135,7 +136,7 @@ struct Context {
     bool ready = false;
     int sm_count = 0;
     DevBuf img, entT, flags, pos, scan_tmp, pool, D, cf, ci, A, rc, part, best, split,
-        split_pos, act0, act1, codes_tmp, codes_out, cellmap, cellflag, cellrank, H,
+        split_pos, act0, act1, codes_tmp, codes_out, cellmap, cellflag, cellrank, H, gbest,
         dec0, dec1, scal;
     Scalars* host_scal = nullptr;  // pinned
     static constexpr int kEntTable = 4097;
@@ -144,9 +145,13 @@ struct Context {
 std::mutex g_ctx_mu;
 Context* g_ctx[64] = {};
 
+thread_local char g_last_error[160] = "";
+
 int to_status(cudaError_t e)
 {
     if (e == cudaSuccess) return FIC_OK;
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s", cudaGetErrorName(e),
+             cudaGetErrorString(e));
     if (e == cudaErrorMemoryAllocation) return FIC_ENOMEM;
     return FIC_ECUDA;
 }
@@ -240,7 +245,7 @@ StepParams make_step(const fic_sset& s, int n)
     sp.n = n;
     sp.q = s.q;
     sp.ns = s.n_s;
-    sp.cw = (int)round_up(1 + s.n_s, 4);
+    sp.cw = 1 + s.n_s;  // m_c and one beta per S, in groups of 4 columns
     for (int i = 0; i < s.n_s; ++i) {
         sp.p[i] = s.p[i];
         sp.kf[i] = (float)(8LL * s.p[i] * s.q);
@@ -294,20 +299,34 @@ int build_pool(Context* c, Launcher& L, const uint8_t* dimg, int N, int B, int L
     return FIC_OK;
 }
 
+// Column chunking of the contraction: work items are (128-row M tile,
+// chunk of column tiles).  Picks the chunk count that minimises the
+// estimated makespan over `slots` concurrent items (waves x tiles per item,
+// plus a per-item cost of refilling the pipeline).
 void choose_chunks(int engine, int sm_count, int64_t rows_pad, int64_t cols_pad, int* n_chunks,
                    int* per_chunk)
 {
     const int64_t n_mtiles = rows_pad / kMTile;
     const int64_t tile_w = engine == FIC_ENGINE_TENSOR ? kNTile : 128;
     const int64_t n_ct = cols_pad / tile_w;
-    const int64_t target = engine == FIC_ENGINE_TENSOR ? 4LL * sm_count : 8LL * sm_count;
-    int64_t nc = (target + n_mtiles - 1) / n_mtiles;
-    if (nc < 1) nc = 1;
-    if (nc > n_ct) nc = n_ct;
-    int64_t per = (n_ct + nc - 1) / nc;
-    nc = (n_ct + per - 1) / per;
-    *n_chunks = (int)nc;
-    *per_chunk = (int)per;
+    const int64_t slots = sm_count;
+    const double item_cost = 2.0;  // in tiles
+    int64_t best_nc = 1;
+    double best = 1e300;
+    const int64_t max_nc = n_ct < 4096 ? n_ct : 4096;
+    for (int64_t nc = 1; nc <= max_nc; ++nc) {
+        const int64_t per = (n_ct + nc - 1) / nc;
+        const int64_t ncs = (n_ct + per - 1) / per;
+        if (ncs != nc) continue;
+        const int64_t waves = (n_mtiles * nc + slots - 1) / slots;
+        const double cost = (double)waves * ((double)per + item_cost);
+        if (cost < best - 1e-9) {
+            best = cost;
+            best_nc = nc;
+        }
+    }
+    *n_chunks = (int)best_nc;
+    *per_chunk = (int)((n_ct + best_nc - 1) / best_nc);
 }
 
 int encode_impl(const uint8_t* img, const fic_params* p, fic_code* codes_out, int64_t codes_cap,
@@ -399,10 +418,11 @@ int encode_impl(const uint8_t* img, const fic_params* p, fic_code* codes_out, in
         FIC_TRY(c->scan_tmp.ensure(sizeof(uint32_t) * scan_tmp_words(R)));
 
         FIC_TRY(cudaMemsetAsync(&ds->vd_max, 0, sizeof(unsigned long long), s));
+        FIC_TRY(cudaMemsetAsync(&ds->vd_min_key, 0xff, sizeof(unsigned long long), s));
         L.begin(FIC_K_GATHER);
         FIC_TRY(launch_gather(dimg, N, B, Lstep, per, pool_xy, dn, cols_pad, K, sp,
                               c->D.as<__half>(), c->cf.as<float>(), c->ci.as<ColExact>(),
-                              &ds->vd_max, s));
+                              &ds->vd_max, &ds->vd_min_key, s));
         L.end(1, 0.0, (double)cols_pad * (2.0 * K + 4.0 * sp.cw + 8.0) + (double)dn * 4.0 * n);
 
         L.begin(FIC_K_RANGE_PREP);
@@ -414,9 +434,12 @@ int encode_impl(const uint8_t* img, const fic_params* p, fic_code* codes_out, in
         if (dn > 0) {
             int per_chunk = 0;
             choose_chunks(p->engine, c->sm_count, rows_pad, cols_pad, &n_chunks, &per_chunk);
-            // the tensor engine writes one partial per chunk and column half
-            n_parts = p->engine == FIC_ENGINE_TENSOR ? 2 * n_chunks : n_chunks;
+            // the tensor engine writes one partial per chunk and column slice
+            n_parts = p->engine == FIC_ENGINE_TENSOR ? contract_tc_parts_per_chunk() * n_chunks
+                                                     : n_chunks;
             FIC_TRY(c->part.ensure(sizeof(Best) * R * n_parts));
+            FIC_TRY(c->gbest.ensure(sizeof(long long) * rows_pad));
+            FIC_TRY(cudaMemsetAsync(c->gbest.p, 0x7f, sizeof(long long) * rows_pad, s));
             ContractArgs a;
             a.A = c->A.as<__half>();
             a.rows_pad = rows_pad;
@@ -431,6 +454,7 @@ int encode_impl(const uint8_t* img, const fic_params* p, fic_code* codes_out, in
             a.n_chunks = n_chunks;
             a.ctiles_per_chunk = per_chunk;
             a.part = c->part.as<Best>();
+            a.gbest = c->gbest.as<long long>();
             a.sp = sp;
             a.err = &ds->err;
             a.grid_ctas = c->sm_count;
@@ -452,7 +476,7 @@ int encode_impl(const uint8_t* img, const fic_params* p, fic_code* codes_out, in
 
         L.begin(FIC_K_SPLIT);
         FIC_TRY(launch_split_decide(c->part.as<Best>(), n_parts, c->rc.as<RowConst>(), (int)R, n,
-                                    sp.q, e16, last, (int)dn, c->best.as<Best>(),
+                                    sp, e16, last, (int)dn, &ds->vd_min_key, c->best.as<Best>(),
                                     c->split.as<uint32_t>(), s));
         int nl = 0;
         FIC_TRY(launch_scan(c->split.as<uint32_t>(), c->split_pos.as<uint32_t>(), R,
@@ -542,6 +566,8 @@ const char* fic_strerror(int status)
 }
 
 const char* fic_version(void) { return "fic-gb300 0.1 (sm_103a)"; }
+
+const char* fic_last_error(void) { return g_last_error; }
 
 int fic_encode_ex(const uint8_t* img, const fic_params* p, fic_code* codes_out, int64_t codes_cap,
                   fic_result* out, void* stream)

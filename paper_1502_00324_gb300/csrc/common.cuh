@@ -64,6 +64,14 @@ struct RowConst {       // one per active range
     float delta;        // bound on |filter - h/n| over all candidates
 };
 
+// A flat range (all pixels equal, Vr = 0) has Crd = 0 against every domain,
+// so h = p^2 Vd for every candidate: its best mapping is the pool's smallest
+// Vd, resolved from one pool-wide key instead of in the contraction.
+__host__ __device__ inline bool range_is_flat(const RowConst& r, int n)
+{
+    return (long long)n * r.sr2 == (long long)r.sr * r.sr;
+}
+
 struct ColExact {       // one per pool domain
     int sd;             // sum d'
     int sd2;            // sum d'^2 (<= 256 * 1020^2 < 2^31)
@@ -77,7 +85,7 @@ struct Best {
     unsigned pad;
 };
 
-constexpr long long kNoCandidate = 0x7fffffffffffffffLL;
+constexpr long long kNoCandidate = 0x7f7f7f7f7f7f7f7fLL;  // byte-fill value: memset 0x7f
 
 __host__ __device__ inline unsigned pack_idx(unsigned c, unsigned k, unsigned s)
 {
@@ -100,9 +108,10 @@ __device__ __forceinline__ long long exact_h(int cprime, int sr, int sd, int sd2
 
 // ---------------------------------------------------------------------------
 // FP32 filter.  For column c and S_s = p_s/q the filter value is
-//   f = fma(8 p q, t, beta_s),  t = fma(a, m_c, -C'),
-// with m_c = sum D'/n (exact), beta_s = fl(p^2 Vd / n).  Exactly,
-// t = -Crd/n and f = h/n; each of the three roundings is relative 2^-24, so
+//   f = fma(-8 p q, t', beta_s),  t' = fma(-a, m_c, C'),
+// with a = sum A' (exact), m_c = sum D'/n (exact), beta_s = fl(p^2 Vd / n).
+// Exactly, t' = Crd/n and f = h/n; each of the three roundings is relative
+// 2^-24, so
 //   |f - h/n| <= (2u + u^2) (8 p q |Crd|/n + p^2 Vd/n),  u = 2^-24,
 // and |Crd| <= sqrt(Vr Vd) (Cauchy-Schwarz).  RowConst.delta holds twice
 // that bound, maximised over the step's S set and the pool's largest Vd.
@@ -113,7 +122,7 @@ struct StepParams {
     int n;              // B*B
     int q;
     int ns;             // number of S values
-    int cw;             // floats per column in the constant table (1 + ns, padded to 4)
+    int cw;             // constants per column: m_c and one beta per S (1 + ns)
     int p[16];
     float kf[16];       // 8 p q
 };

@@ -6,7 +6,8 @@
 // D' rows are pool domains holding d' - 510.  Both come in the tile layout of
 // common.cuh.  One block owns a 128-row M tile (16 ranges x 8 isometries)
 // and a chunk of 128-column tiles; thread (ty, tx) owns range ty of the tile
-// (its 8 isometry rows) and columns tx, tx+16, ..., tx+112 of each tile.
+// (its 8 isometry rows) and the column groups 4tx..4tx+3 and 64+4tx..64+4tx+3
+// of each tile.
 #include "epilogue.cuh"
 #include "kernels.h"
 
@@ -19,21 +20,27 @@ contract_plain_kernel(const __half* __restrict__ A, int64_t rows_pad,
                       const float* __restrict__ cf, const ColExact* __restrict__ ci,
                       const RowConst* __restrict__ rc, int R, int dn, int ctiles_per_chunk,
                       int n_ctiles, int n_chunks, Best* __restrict__ part,
-                      const __grid_constant__ StepParams sp)
+                      long long* __restrict__ gbest, const __grid_constant__ StepParams sp)
 {
     __shared__ __align__(16) int sA[16][128];
     __shared__ __align__(16) int sD[16][128];
     const int tid = threadIdx.x;
     const int ty = tid >> 4, tx = tid & 15;
-    const int mtile = blockIdx.y, chunk = blockIdx.x;
+    // M tiles vary fastest, so the blocks running together share one column
+    // chunk and a range's earlier chunks finish before its later ones start
+    const int mtile = blockIdx.x, chunk = blockIdx.y;
     const int range = mtile * kRangesPerTile + ty;
-    const bool valid = range < R;
-    RowConst r = valid ? rc[range] : RowConst{0, 0, 0.f, 0.f};
+    const RowConst r = range < R ? rc[range] : RowConst{0, 0, 0.f, 0.f};
+    // flat ranges are resolved in the split step (h = p^2 Vd)
+    const bool valid = range < R && !range_is_flat(r, sp.n);
     const float inv_n = 1.0f / (float)sp.n;
 
     RowState st[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) row_state_init(st[i]);
+    for (int i = 0; i < 8; ++i) {
+        row_state_init(st[i]);
+        if (valid) row_state_seed(st[i], gbest + (int64_t)range * 8 + i, inv_n, r.delta);
+    }
 
     const int ct0 = chunk * ctiles_per_chunk;
     const int ct1 = min(n_ctiles, ct0 + ctiles_per_chunk);
@@ -66,9 +73,9 @@ contract_plain_kernel(const __half* __restrict__ A, int64_t rows_pad,
                 const int4 a0 = *reinterpret_cast<const int4*>(&sA[k][ty * 8]);
                 const int4 a1 = *reinterpret_cast<const int4*>(&sA[k][ty * 8 + 4]);
                 const int av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-                int dv[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) dv[j] = sD[k][tx + 16 * j];
+                const int4 d0 = *reinterpret_cast<const int4*>(&sD[k][4 * tx]);
+                const int4 d1 = *reinterpret_cast<const int4*>(&sD[k][64 + 4 * tx]);
+                const int dv[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
 #pragma unroll
@@ -82,11 +89,14 @@ contract_plain_kernel(const __half* __restrict__ A, int64_t rows_pad,
                 float x[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) x[j] = (float)acc[i][j];
-                epi_block<NS, 8>(st[i], x, cf, ct * 128 + tx, ct * 128 + tx, 16, (unsigned)i, r.a,
-                                 r.delta, inv_n, r.sr, ci, dn, &sp);
+                epi_groups<NS, 2>(st[i], x, cf, ct * 32 + tx, 16, 0, (unsigned)i, -r.a, r.delta,
+                                  inv_n, r.sr, ci, dn, &sp);
             }
         }
     }
+    if (valid)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) row_state_publish(st[i], gbest + (int64_t)range * 8 + i);
     // best over the 8 isometries held by this thread, then over the 16 threads
     long long h = st[0].h;
     unsigned idx = st[0].idx;
@@ -110,13 +120,13 @@ contract_plain_kernel(const __half* __restrict__ A, int64_t rows_pad,
 template <int K>
 static cudaError_t launch_plain_k(const ContractArgs& a, cudaStream_t s)
 {
-    dim3 grid(a.n_chunks, a.rows_pad / kMTile);
+    dim3 grid((unsigned)(a.rows_pad / kMTile), a.n_chunks);
     const int n_ctiles = (int)(a.cols_pad / 128);
     const int per = a.ctiles_per_chunk;
 #define FIC_PLAIN_CASE(NSV)                                                              \
     contract_plain_kernel<K, NSV><<<grid, 256, 0, s>>>(                                  \
         a.A, a.rows_pad, a.D, a.cols_pad, a.cf, a.ci, a.rc, a.R, a.dn, per, n_ctiles,   \
-        a.n_chunks, a.part, a.sp)
+        a.n_chunks, a.part, a.gbest, a.sp)
     switch (a.sp.ns) {
         case 1: FIC_PLAIN_CASE(1); break;
         case 2: FIC_PLAIN_CASE(2); break;

@@ -18,10 +18,13 @@
 //               accumulators); one thread issues tcgen05.mma per K step and
 //               tcgen05.commit to release stages and publish accumulators;
 //   warps 2-9   epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (one
-//               row per thread) for one half of the 256 columns with
-//               tcgen05.ld, runs the filter/exact argmin of epilogue.cuh,
-//               and releases the accumulator.
-// Every mbarrier wait is bounded (globaltimer); on expiry the kernel records
+//               row per thread) for one half of the 256 columns, 64 columns
+//               per tcgen05.ld, hands the accumulator back as soon as the
+//               last chunk is in registers, and runs the filter/exact argmin
+//               of epilogue.cuh.
+// Work items are ordered column-chunk-major, so the CTAs running at one
+// time share a few D' chunks in L2 instead of streaming all of D'.
+// Every mbarrier wait is bounded (cycle counter); on expiry the kernel records
 // FIC_ETIMEOUT in the error word, drains its own copies and MMAs, frees TMEM
 // and returns.
 #include <cstdio>
@@ -66,27 +69,24 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-__device__ __forceinline__ uint64_t global_ns()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
+constexpr long long kWaitCycles = 8000000000LL;   // ~4 s at 2 GHz: far above any stage wait
+constexpr long long kDrainCycles = 400000000LL;   // ~0.2 s for the drain after an error
 
-constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s: far above any stage wait
-constexpr uint64_t kDrainNs = 100000000ull;  // 0.1 s for the drain after an error
-
-// Bounded parity wait.  Returns false when the limit passed or another
+// Bounded parity wait.  try_wait suspends the thread in hardware between
+// polls; the cycle counter and the error word are only looked at every 256
+// unsuccessful polls.  Returns false when the limit passed or another
 // thread already recorded an error.
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, uint64_t limit)
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, long long limit)
 {
-    if (mbar_try(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
+    long long t0 = 0;
     for (uint32_t i = 1;; ++i) {
         if (mbar_try(bar, parity)) return true;
-        if ((i & 63) == 0) {
+        if ((i & 255) == 0) {
             if (*(volatile int*)err) return false;
-            if (global_ns() - t0 > limit) {
+            const long long now = clock64();
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > limit) {
                 atomicCAS(err, 0, kErrTimeout);
                 return false;
             }
@@ -133,34 +133,44 @@ __device__ __forceinline__ void tc_mma_f16(uint32_t d_tmem, uint64_t adesc, uint
         : "memory");
 }
 
-// 32 lanes x 32 consecutive FP32 columns; thread i gets lane (base lane + i).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+// 32 lanes x 64 consecutive FP32 columns; thread i gets lane (base lane + i).
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64])
 {
-    uint32_t r[32];
+    uint32_t r[64];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-          "=r"(r[31])
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
         : "r"(taddr));
     // the wait takes the registers as operands so no use moves above it
-    asm volatile(
-        "tcgen05.wait::ld.sync.aligned;"
-        : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
-          "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]),
-          "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]),
-          "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]),
-          "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]),
-          "+r"(r[31])
-        :
-        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31]), "+r"(r[32]), "+r"(r[33]), "+r"(r[34]), "+r"(r[35]), "+r"(r[36]), "+r"(r[37]), "+r"(r[38]), "+r"(r[39]), "+r"(r[40]), "+r"(r[41]), "+r"(r[42]), "+r"(r[43]), "+r"(r[44]), "+r"(r[45]), "+r"(r[46]), "+r"(r[47]), "+r"(r[48]), "+r"(r[49]), "+r"(r[50]), "+r"(r[51]), "+r"(r[52]), "+r"(r[53]), "+r"(r[54]), "+r"(r[55]), "+r"(r[56]), "+r"(r[57]), "+r"(r[58]), "+r"(r[59]), "+r"(r[60]), "+r"(r[61]), "+r"(r[62]), "+r"(r[63])
+                 :
+                 : "memory");
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 32 lanes x 32 consecutive FP32 columns, issued without waiting: the
+// registers of v are written asynchronously and may be read only after
+// tmem_wait32(v).
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, float (&v)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]), "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15]), "=f"(v[16]), "=f"(v[17]), "=f"(v[18]), "=f"(v[19]), "=f"(v[20]), "=f"(v[21]), "=f"(v[22]), "=f"(v[23]), "=f"(v[24]), "=f"(v[25]), "=f"(v[26]), "=f"(v[27]), "=f"(v[28]), "=f"(v[29]), "=f"(v[30]), "=f"(v[31])
+        : "r"(taddr));
+}
+
+// Waits for this thread's outstanding tcgen05.ld; v is an operand so that no
+// use of it moves above the wait.
+__device__ __forceinline__ void tmem_wait32(float (&v)[32])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]), "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]), "+f"(v[13]), "+f"(v[14]), "+f"(v[15]), "+f"(v[16]), "+f"(v[17]), "+f"(v[18]), "+f"(v[19]), "+f"(v[20]), "+f"(v[21]), "+f"(v[22]), "+f"(v[23]), "+f"(v[24]), "+f"(v[25]), "+f"(v[26]), "+f"(v[27]), "+f"(v[28]), "+f"(v[29]), "+f"(v[30]), "+f"(v[31])
+                 :
+                 : "memory");
 }
 
 // Shared-memory matrix descriptor, K-major, no swizzle: start address,
@@ -179,8 +189,22 @@ __host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N)
     return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-constexpr int kThreads = 320;
-constexpr int kEpiWarps = 8;
+#ifndef FIC_TC_EPI_WARPS
+#define FIC_TC_EPI_WARPS 8
+#endif
+#ifndef FIC_TC_PIPE
+#define FIC_TC_PIPE 0
+#endif
+constexpr int kEpiWarps = FIC_TC_EPI_WARPS;     // epilogue warps, 4 per lane quadrant group
+constexpr int kThreads = 32 * (2 + kEpiWarps);
+constexpr int kColsPerEpiWarp = 256 * 4 / kEpiWarps;
+constexpr int kEpiBlocks = kColsPerEpiWarp / 32;      // 32-column blocks per tile
+constexpr int kPartsPerChunk = kEpiWarps / 4;         // partials per (range, column chunk)
+// Registers live in four 16K-entry files, one per SM sub-partition, and the
+// warps of a block are dealt round-robin to the sub-partitions.
+constexpr int kWarpsPerSubPartition = (kThreads / 32 + 3) / 4;
+constexpr int kMaxRegsRaw = 16384 / (32 * kWarpsPerSubPartition) / 8 * 8;
+constexpr int kMaxRegs = kMaxRegsRaw > 255 ? 255 : kMaxRegsRaw;
 constexpr uint32_t kTmemCols = 512;
 
 struct TcParams {
@@ -192,12 +216,13 @@ struct TcParams {
     const ColExact* ci;
     const RowConst* rc;
     Best* part;
+    long long* gbest;
     int* err;
-    int R, dn, n_chunks, per_chunk, n_ct, n_items, nstage;
+    int R, dn, n_chunks, per_chunk, n_ct, n_mtiles, n_items, nstage, ncf;
 };
 
 template <int K, int NS>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __maxnreg__(kMaxRegs)
 contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ StepParams sp)
 {
     constexpr int KB = K < 64 ? K : 64;
@@ -208,24 +233,26 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
     constexpr uint32_t kIdesc = idesc_f16_f32(128, 256);
     const uint32_t cf_bytes = 256u * (uint32_t)sp.cw * 4u;
     const int nstage = P.nstage;
+    const int ncf = P.ncf;  // column-constant tiles in flight (ring)
 
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* sA = smem;
     uint8_t* sB = sA + NKB * kAKBBytes;
     uint8_t* sCF = sB + (size_t)nstage * kBStageBytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sCF + 2 * cf_bytes);
-    // barrier slots
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sCF + (size_t)ncf * cf_bytes);
+    // barrier slots: A tile, D stages, accumulators, constant tiles, drain
     const uint32_t b_base = smem_u32(bars);
     const uint32_t a_full = b_base, a_empty = b_base + 8;
     auto full = [&](int s) { return b_base + 16 + 8u * s; };
     auto empty = [&](int s) { return b_base + 16 + 8u * (nstage + s); };
-    const uint32_t b_tail = b_base + 16 + 16u * nstage;
-    auto tfull = [&](int a) { return b_tail + 8u * a; };
-    auto tempty = [&](int a) { return b_tail + 16 + 8u * a; };
-    auto cff = [&](int a) { return b_tail + 32 + 8u * a; };
-    auto cfe = [&](int a) { return b_tail + 48 + 8u * a; };
-    const uint32_t drain = b_tail + 64;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 + 2 * nstage + 9);
+    const uint32_t b_acc = b_base + 16 + 16u * nstage;
+    auto tfull = [&](int a) { return b_acc + 8u * a; };
+    auto tempty = [&](int a) { return b_acc + 16 + 8u * a; };
+    const uint32_t b_cf = b_acc + 32;
+    auto cff = [&](int c) { return b_cf + 8u * c; };
+    auto cfe = [&](int c) { return b_cf + 8u * (ncf + c); };
+    const uint32_t drain = b_cf + 16u * ncf;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 + 2 * nstage + 4 + 2 * ncf + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -238,8 +265,10 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
         for (int a = 0; a < 2; ++a) {
             mbar_init(tfull(a), 1);
             mbar_init(tempty(a), kEpiWarps);
-            mbar_init(cff(a), 1);
-            mbar_init(cfe(a), kEpiWarps);
+        }
+        for (int c = 0; c < ncf; ++c) {
+            mbar_init(cff(c), 1);
+            mbar_init(cfe(c), kEpiWarps);
         }
         mbar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -262,10 +291,10 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
             int64_t it = 0, tcount = 0, icount = 0;
             bool ok = true;
             for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
-                const int mtile = item / P.n_chunks, chunk = item % P.n_chunks;
+                const int chunk = item / P.n_mtiles, mtile = item % P.n_mtiles;
                 const int ct0 = chunk * P.per_chunk;
                 const int ct1 = min(P.n_ct, ct0 + P.per_chunk);
-                if (!(ok = mbar_wait(a_empty, (uint32_t)((icount & 1) ^ 1), err, kWaitNs))) break;
+                if (!(ok = mbar_wait(a_empty, (uint32_t)((icount & 1) ^ 1), err, kWaitCycles))) break;
                 mbar_expect_tx(a_full, NKB * kAKBBytes);
                 for (int kb = 0; kb < NKB; ++kb)
                     bulk_g2s(smem_u32(sA + kb * kAKBBytes),
@@ -273,16 +302,16 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
                              kAKBBytes, a_full);
                 ++icount;
                 for (int ct = ct0; ct < ct1 && ok; ++ct) {
-                    const int acc = (int)(tcount & 1);
-                    const uint32_t ph = (uint32_t)((tcount >> 1) & 1);
-                    if (!(ok = mbar_wait(cfe(acc), ph ^ 1, err, kWaitNs))) break;
-                    mbar_expect_tx(cff(acc), cf_bytes);
-                    bulk_g2s(smem_u32(sCF + acc * cf_bytes), P.cf + (int64_t)ct * 256 * sp.cw,
-                             cf_bytes, cff(acc));
+                    const int cb = (int)(tcount % ncf);
+                    const uint32_t cph = (uint32_t)((tcount / ncf) & 1);
+                    if (!(ok = mbar_wait(cfe(cb), cph ^ 1, err, kWaitCycles))) break;
+                    mbar_expect_tx(cff(cb), cf_bytes);
+                    bulk_g2s(smem_u32(sCF + (size_t)cb * cf_bytes), P.cf + (int64_t)ct * 256 * sp.cw,
+                             cf_bytes, cff(cb));
                     for (int kb = 0; kb < NKB; ++kb) {
                         const int s = (int)(it % nstage);
                         const uint32_t sph = (uint32_t)((it / nstage) & 1);
-                        if (!(ok = mbar_wait(empty(s), sph ^ 1, err, kWaitNs))) break;
+                        if (!(ok = mbar_wait(empty(s), sph ^ 1, err, kWaitCycles))) break;
                         mbar_expect_tx(full(s), kBStageBytes);
                         bulk_g2s(smem_u32(sB + (size_t)s * kBStageBytes),
                                  P.D + ((int64_t)kb * P.cols_pad * KB + (int64_t)ct * 256 * KB),
@@ -296,10 +325,10 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
                 // drain: let every copy this thread armed land before exit
                 for (int64_t j = (it > nstage ? it - nstage : 0); j < it; ++j)
                     mbar_wait(full((int)(j % nstage)), (uint32_t)((j / nstage) & 1), err + 1,
-                              kDrainNs);
-                if (icount > 0) mbar_wait(a_full, (uint32_t)((icount - 1) & 1), err + 1, kDrainNs);
-                for (int64_t j = (tcount > 2 ? tcount - 2 : 0); j < tcount; ++j)
-                    mbar_wait(cff((int)(j & 1)), (uint32_t)((j >> 1) & 1), err + 1, kDrainNs);
+                              kDrainCycles);
+                if (icount > 0) mbar_wait(a_full, (uint32_t)((icount - 1) & 1), err + 1, kDrainCycles);
+                for (int64_t j = (tcount > ncf ? tcount - ncf : 0); j < tcount; ++j)
+                    mbar_wait(cff((int)(j % ncf)), (uint32_t)((j / ncf) & 1), err + 1, kDrainCycles);
             }
         }
     } else if (warp == 1) {
@@ -308,21 +337,21 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
             int64_t it = 0, tcount = 0, icount = 0;
             bool ok = true;
             for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
-                const int chunk = item % P.n_chunks;
+                const int chunk = item / P.n_mtiles;
                 const int ct0 = chunk * P.per_chunk;
                 const int ct1 = min(P.n_ct, ct0 + P.per_chunk);
-                if (!(ok = mbar_wait(a_full, (uint32_t)(icount & 1), err, kWaitNs))) break;
+                if (!(ok = mbar_wait(a_full, (uint32_t)(icount & 1), err, kWaitCycles))) break;
                 tc_fence_after();
                 for (int ct = ct0; ct < ct1 && ok; ++ct) {
                     const int acc = (int)(tcount & 1);
                     const uint32_t ph = (uint32_t)((tcount >> 1) & 1);
-                    if (!(ok = mbar_wait(tempty(acc), ph ^ 1, err, kWaitNs))) break;
+                    if (!(ok = mbar_wait(tempty(acc), ph ^ 1, err, kWaitCycles))) break;
                     tc_fence_after();
                     const uint32_t d_tmem = tmem_base + (uint32_t)acc * 256u;
                     for (int kb = 0; kb < NKB; ++kb) {
                         const int s = (int)(it % nstage);
                         const uint32_t sph = (uint32_t)((it / nstage) & 1);
-                        if (!(ok = mbar_wait(full(s), sph, err, kWaitNs))) break;
+                        if (!(ok = mbar_wait(full(s), sph, err, kWaitCycles))) break;
                         tc_fence_after();
                         const uint32_t a0 = smem_u32(sA + kb * kAKBBytes);
                         const uint32_t b0 = smem_u32(sB + (size_t)s * kBStageBytes);
@@ -344,54 +373,98 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
             }
             // every issued MMA has finished before TMEM is released
             tc_commit(drain);
-            mbar_wait(drain, 0, err + 1, kWaitNs);
+            mbar_wait(drain, 0, err + 1, kWaitCycles);
         }
     } else {
         // ------------------------------------------------------------ epilogue
         const int e = warp - 2;
-        const int quad = warp & 3;
-        const int hsel = e >> 2;
+        const int quad = warp & 3;          // TMEM lanes 32 quad .. 32 quad + 31
+        const int cq = e >> 2;              // column slice cq of a tile
         const float inv_n = 1.0f / (float)sp.n;
         int64_t tcount = 0;
         bool ok = true;
         for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
-            const int mtile = item / P.n_chunks, chunk = item % P.n_chunks;
+            const int chunk = item / P.n_mtiles, mtile = item % P.n_mtiles;
             const int ct0 = chunk * P.per_chunk;
             const int ct1 = min(P.n_ct, ct0 + P.per_chunk);
             const int row = mtile * 128 + quad * 32 + lane;
             const int range = row >> 3;
             const unsigned iso = (unsigned)(row & 7);
-            const bool valid = range < P.R;
-            const RowConst r = valid ? P.rc[range] : RowConst{0, 0, 0.f, 0.f};
+            const RowConst r = range < P.R ? P.rc[range] : RowConst{0, 0, 0.f, 0.f};
+            // flat ranges are resolved in the split step (h = p^2 Vd)
+            const bool valid = range < P.R && !range_is_flat(r, sp.n);
             RowState st;
             row_state_init(st);
+            if (valid) row_state_seed(st, P.gbest + row, inv_n, r.delta);
             for (int ct = ct0; ct < ct1; ++ct) {
                 const int acc = (int)(tcount & 1);
                 const uint32_t ph = (uint32_t)((tcount >> 1) & 1);
-                if (!(ok = mbar_wait(tfull(acc), ph, err, kWaitNs))) break;
-                if (!(ok = mbar_wait(cff(acc), ph, err, kWaitNs))) break;
+                const int cb = (int)(tcount % ncf);
+                const uint32_t cph = (uint32_t)((tcount / ncf) & 1);
+                if (!(ok = mbar_wait(tfull(acc), ph, err, kWaitCycles))) break;
+                if (!(ok = mbar_wait(cff(cb), cph, err, kWaitCycles))) break;
                 tc_fence_after();
-                const float* cfs = reinterpret_cast<const float*>(sCF + acc * cf_bytes);
+                const float* cfs = reinterpret_cast<const float*>(sCF + (size_t)cb * cf_bytes);
+                const uint32_t tb = tmem_base + ((uint32_t)(quad * 32) << 16) +
+                                    (uint32_t)(acc * 256 + cq * kColsPerEpiWarp);
+#if FIC_TC_PIPE
+                // double-buffered 32-column loads: block b+1 streams in while
+                // pass 1 scores block b; the wait comes before the (rare) pass 2
+                // so no register of an unfinished load is live across its calls
+                float xa[32], xb[32];
+                __syncwarp();
+                tmem_ld32_issue(tb, xa);
+                tmem_wait32(xa);
+#pragma unroll
+                for (int b = 0; b < kEpiBlocks; ++b) {
+                    float(&cur)[32] = (b & 1) ? xb : xa;
+                    float(&nxt)[32] = (b & 1) ? xa : xb;
+                    const bool more = b + 1 < kEpiBlocks;
+                    if (more) {
+                        __syncwarp();
+                        tmem_ld32_issue(tb + 32u * (b + 1), nxt);
+                    } else {
+                        // the accumulator is in registers: hand TMEM back to the MMA
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(tempty(acc));
+                    }
+                    const int g0 = (cq * kColsPerEpiWarp + 32 * b) / 4;
+                    const float mn = valid ? epi_pass1<NS, 8>(cur, cfs, g0, 1, -r.a, &sp)
+                                           : __int_as_float(0x7f800000);
+                    if (more) {
+                        __syncwarp();
+                        tmem_wait32(nxt);
+                    }
+                    if (mn <= st.thr)
+                        epi_pass2<NS, 8>(st, cur, mn, cfs, g0, 1, ct * 256, iso, -r.a, r.delta,
+                                         inv_n, r.sr, P.ci, P.dn, &sp);
+                }
+#else
 #pragma unroll 1
-                for (int cb = 0; cb < 4; ++cb) {
-                    const int cit = hsel * 128 + cb * 32;
+                for (int b = 0; b < kEpiBlocks; ++b) {
                     float x[32];
                     __syncwarp();
-                    tmem_ld32(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * 256 + cit),
-                              x);
+                    tmem_ld32_issue(tb + 32u * b, x);
+                    tmem_wait32(x);
+                    if (b == kEpiBlocks - 1) {
+                        // the accumulator is in registers: hand TMEM back to the MMA
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(tempty(acc));
+                    }
                     if (valid)
-                        epi_block<NS, 32>(st, x, cfs, cit, ct * 256 + cit, 1, iso, r.a, r.delta,
-                                          inv_n, r.sr, P.ci, P.dn, &sp);
+                        epi_groups<NS, 8>(st, x, cfs, (cq * kColsPerEpiWarp + 32 * b) / 4, 1,
+                                          ct * 256, iso, -r.a, r.delta, inv_n, r.sr, P.ci, P.dn,
+                                          &sp);
                 }
-                tc_fence_before();
+#endif
                 __syncwarp();
-                if (lane == 0) {
-                    mbar_arrive(tempty(acc));
-                    mbar_arrive(cfe(acc));
-                }
+                if (lane == 0) mbar_arrive(cfe(cb));
                 ++tcount;
             }
             if (!ok) break;
+            if (valid) row_state_publish(st, P.gbest + row);
             // best over the 8 isometries of each range (lanes 8j .. 8j+7)
             long long h = st.h;
             unsigned idx = st.idx;
@@ -403,7 +476,7 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
                 b.h = h;
                 b.idx = idx;
                 b.pad = 0;
-                P.part[(int64_t)range * (2 * P.n_chunks) + 2 * chunk + hsel] = b;
+                P.part[(int64_t)range * (kPartsPerChunk * P.n_chunks) + kPartsPerChunk * chunk + cq] = b;
             }
         }
     }
@@ -423,17 +496,19 @@ constexpr size_t kSmemBudget = 220 * 1024;
 constexpr size_t kSmemMinForOneCta = 120 * 1024;  // > half an SM: one CTA per SM
 
 template <int K>
-size_t tc_layout(int cw, int* nstage_out)
+size_t tc_layout(int cw, int* nstage_out, int* ncf_out)
 {
     constexpr int KB = K < 64 ? K : 64;
     const size_t a_bytes = (size_t)128 * K * 2;
     const size_t stage = (size_t)256 * KB * 2;
-    const size_t cf = (size_t)2 * 256 * cw * 4;
-    const size_t fixed = a_bytes + cf + 1024;
+    const size_t cf_tile = (size_t)256 * cw * 4;
+    const int ncf = cf_tile <= 4096 ? 8 : 2;  // deep ring for the usual 1-3 S values
+    const size_t fixed = a_bytes + (size_t)ncf * cf_tile + 1024;
     int ns = (int)((kSmemBudget - fixed) / stage);
     if (ns > 8) ns = 8;
     if (ns < 2) ns = 2;
     *nstage_out = ns;
+    *ncf_out = ncf;
     size_t total = fixed + (size_t)ns * stage;
     if (total < kSmemMinForOneCta) total = kSmemMinForOneCta;
     return total;
@@ -442,8 +517,8 @@ size_t tc_layout(int cw, int* nstage_out)
 template <int K, int NS>
 cudaError_t launch_tc_kns(const ContractArgs& a, cudaStream_t s)
 {
-    int nstage = 0;
-    const size_t smem = tc_layout<K>(a.sp.cw, &nstage);
+    int nstage = 0, ncf = 0;
+    const size_t smem = tc_layout<K>(a.sp.cw, &nstage, &ncf);
     auto kern = contract_tc_kernel<K, NS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
@@ -457,14 +532,17 @@ cudaError_t launch_tc_kns(const ContractArgs& a, cudaStream_t s)
     P.ci = a.ci;
     P.rc = a.rc;
     P.part = a.part;
+    P.gbest = a.gbest;
     P.err = a.err;
     P.R = a.R;
     P.dn = a.dn;
     P.n_chunks = a.n_chunks;
     P.per_chunk = a.ctiles_per_chunk;
     P.n_ct = (int)(a.cols_pad / 256);
-    P.n_items = (int)(a.rows_pad / 128) * a.n_chunks;
+    P.n_mtiles = (int)(a.rows_pad / 128);
+    P.n_items = P.n_mtiles * a.n_chunks;
     P.nstage = nstage;
+    P.ncf = ncf;
     const int grid = P.n_items < a.grid_ctas ? P.n_items : a.grid_ctas;
     kern<<<grid, kThreads, smem, s>>>(P, a.sp);
     return cudaGetLastError();
@@ -493,13 +571,15 @@ cudaError_t launch_contract_tc(const ContractArgs& a, cudaStream_t s)
     }
 }
 
+int contract_tc_parts_per_chunk() { return kPartsPerChunk; }
+
 size_t contract_tc_smem_bytes(int K)
 {
-    int ns = 0;
+    int ns = 0, ncf = 0;
     switch (K) {
-        case 16: return tc_layout<16>(4, &ns);
-        case 64: return tc_layout<64>(4, &ns);
-        case 256: return tc_layout<256>(4, &ns);
+        case 16: return tc_layout<16>(3, &ns, &ncf);
+        case 64: return tc_layout<64>(3, &ns, &ncf);
+        case 256: return tc_layout<256>(3, &ns, &ncf);
         default: return 0;
     }
 }

@@ -7,6 +7,15 @@
 // an FP32 filter f ~ h/n with a proven error bound delta (common.cuh); only
 // candidates that can tie or beat the row's best are re-scored exactly,
 // keeping the lexicographically smallest (h, pool index, isometry, S index).
+//
+// Filter, per element: t' = C' - a m_c (= Crd/n exactly), f_s = beta_s - 8 p q t'.
+// Both are single-rounding FMAs, evaluated two columns at a time with the
+// packed fma.rn.f32x2 (each lane an IEEE round-to-nearest FMA).
+//
+// Column constants are stored in groups of 4 columns: for group g the
+// constant j of its 4 columns is the float4 at cf + (g * cw + j) * 4, with
+// j = 0 for m_c and j = 1 + s for beta_s (cw = 1 + |S|); padded columns
+// carry beta = +inf.
 #pragma once
 
 #include "common.cuh"
@@ -33,51 +42,49 @@ __device__ __forceinline__ float fmin3(float a, float b, float c)
     return r;
 }
 
-// Column constants: cf[c * cw] = m_c (= sum D' / n), cf[c * cw + 1 + s] =
-// beta_s (= fl(p_s^2 Vd / n)); padded columns carry beta = +inf.
-// Returns min over s of the filter values; f[] receives them.
-template <int NS>
-__device__ __forceinline__ float filter_vals(const float* __restrict__ cfc, float a, float x,
-                                             const StepParams& sp, float* f)
+__device__ __forceinline__ uint64_t pk2(float lo, float hi)
 {
-    if constexpr (NS >= 1 && NS <= 3) {
-        const float4 c = *reinterpret_cast<const float4*>(cfc);
-        const float t = __fmaf_rn(a, c.x, -x);
-        f[0] = __fmaf_rn(sp.kf[0], t, c.y);
-        if constexpr (NS == 1) return f[0];
-        f[1] = __fmaf_rn(sp.kf[1], t, c.z);
-        if constexpr (NS == 2) return fminf(f[0], f[1]);
-        f[2] = __fmaf_rn(sp.kf[2], t, c.w);
-        return fminf(f[0], fminf(f[1], f[2]));
-    } else {
-        const float t = __fmaf_rn(a, cfc[0], -x);
-        float m = __int_as_float(0x7f800000);
-        for (int s = 0; s < sp.ns; ++s) {
-            f[s] = __fmaf_rn(sp.kf[s], t, cfc[1 + s]);
-            m = fminf(m, f[s]);
-        }
-        return m;
-    }
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ void upk2(uint64_t v, float& lo, float& hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+// (d.lo, d.hi) = (a.lo * b.lo + c.lo, a.hi * b.hi + c.hi), each rounded once.
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// Filter values of one column (scalar form, same roundings as the packed one).
+__device__ __forceinline__ float col_filter(const float* __restrict__ cg, int e, float na,
+                                            float x, const StepParams& sp, int s)
+{
+    const float tp = __fmaf_rn(na, cg[e], x);                // C' - a m
+    return __fmaf_rn(-sp.kf[s], tp, cg[(1 + s) * 4 + e]);   // beta - 8pq t'
 }
 
 // Exact re-scoring of one column for the S values whose filter passes te.
 // Out of line: it runs rarely, and a call keeps the caller's register
 // arrays statically indexed.
-template <int NS>
-__device__ __noinline__ RowState exact_col(RowState st, float x, const float* __restrict__ cfc,
-                                           int col, unsigned iso, float a, float delta,
+static __device__ __noinline__ RowState exact_col(RowState st, float x, const float* __restrict__ cg,
+                                           int e, int col, unsigned iso, float na, float delta,
                                            float inv_n, int sr, const ColExact* __restrict__ ci,
                                            int dn, const StepParams* __restrict__ spp, float te)
 {
     const StepParams& sp = *spp;
     if (col >= dn) return st;
-    float f[NS == 0 ? 16 : NS];
-    filter_vals<NS>(cfc, a, x, sp, f);
     const ColExact ce = ci[col];
     const int cprime = __float2int_rn(x);
-    const int ns = NS == 0 ? sp.ns : NS;
-    for (int s = 0; s < ns; ++s) {
-        if (!(f[s] <= te)) continue;
+    for (int s = 0; s < sp.ns; ++s) {
+        const float f = col_filter(cg, e, na, x, sp, s);
+        if (!(f <= te)) continue;
         const long long h = exact_h(cprime, sr, ce.sd, ce.sd2, sp.n, sp.p[s], sp.q);
         const unsigned idx = pack_idx((unsigned)col, iso, (unsigned)s);
         if (key_less(h, idx, st.h, st.idx)) {
@@ -90,52 +97,151 @@ __device__ __noinline__ RowState exact_col(RowState st, float x, const float* __
     return st;
 }
 
-// Process NCOL outputs x[j] of one row.  The constants of x[j] are at
-// cf + (cf_col0 + j * cstride) * cw; its pool column is col0 + j * cstride.
-// NS = 1..3 selects the unrolled path; NS = 0 handles any sp.ns <= 16.
-template <int NS, int NCOL>
-__device__ __forceinline__ void epi_block(RowState& st, const float (&x)[NCOL],
-                                          const float* __restrict__ cf, int cf_col0, int col0,
-                                          int cstride, unsigned iso, float a, float delta,
-                                          float inv_n, int sr, const ColExact* __restrict__ ci,
-                                          int dn, const StepParams* __restrict__ spp)
+// Process NG groups of 4 consecutive columns of one row: group g holds
+// x[4g .. 4g+3], its constants start at cf + (g0 + g * gstride) * cw * 4 and
+// its first pool column is (g0 + g * gstride) * 4 + col_base.
+// NS = 1..3 selects the unrolled packed path; NS = 0 handles any |S| <= 16.
+template <int NS, int NG>
+__device__ __forceinline__ float epi_pass1(const float (&x)[4 * NG], const float* __restrict__ cf,
+                                           int g0, int gstride, float na,
+                                           const StepParams* __restrict__ spp)
 {
     const StepParams& sp = *spp;
-    constexpr int NSV = (NS == 0) ? 16 : NS;
-    // pass 1: block minimum of the filter
-    float mn0 = __int_as_float(0x7f800000), mn1 = mn0;
+    const int cw = (NS == 0) ? sp.cw : 1 + NS;
+    // pass 1: block minimum of the filter (four independent min chains)
+    float mn0 = __int_as_float(0x7f800000), mn1 = mn0, mn2 = mn0, mn3 = mn0;
+    if constexpr (NS >= 1 && NS <= 3) {
+        const uint64_t nak = pk2(na, na);
+        uint64_t nk[NS];
 #pragma unroll
-    for (int j = 0; j < NCOL; ++j) {
-        const float* cfc = cf + (size_t)(cf_col0 + j * cstride) * sp.cw;
-        if constexpr (NS == 2) {
-            const float4 c = *reinterpret_cast<const float4*>(cfc);
-            const float t = __fmaf_rn(a, c.x, -x[j]);
-            const float f0 = __fmaf_rn(sp.kf[0], t, c.y);
-            const float f1 = __fmaf_rn(sp.kf[1], t, c.z);
-            if (j & 1) mn1 = fmin3(mn1, f0, f1);
-            else mn0 = fmin3(mn0, f0, f1);
-        } else {
-            float f[NSV];
-            const float m = filter_vals<NS>(cfc, a, x[j], sp, f);
-            if (j & 1) mn1 = fminf(mn1, m);
-            else mn0 = fminf(mn0, m);
+        for (int s = 0; s < NS; ++s) nk[s] = pk2(-sp.kf[s], -sp.kf[s]);
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+            const float4* cg = reinterpret_cast<const float4*>(cf + (size_t)(g0 + g * gstride) * cw * 4);
+            const float4 m = cg[0];
+            const uint64_t t01 = fma2(nak, pk2(m.x, m.y), pk2(x[4 * g], x[4 * g + 1]));
+            const uint64_t t23 = fma2(nak, pk2(m.z, m.w), pk2(x[4 * g + 2], x[4 * g + 3]));
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const float4 b = cg[1 + s];
+                float f0, f1, f2, f3;
+                upk2(fma2(nk[s], t01, pk2(b.x, b.y)), f0, f1);
+                upk2(fma2(nk[s], t23, pk2(b.z, b.w)), f2, f3);
+                if (g & 1) {
+                    mn2 = fmin3(mn2, f0, f1);
+                    mn3 = fmin3(mn3, f2, f3);
+                } else {
+                    mn0 = fmin3(mn0, f0, f1);
+                    mn1 = fmin3(mn1, f2, f3);
+                }
+            }
+        }
+    } else {
+        for (int g = 0; g < NG; ++g) {
+            const float* cg = cf + (size_t)(g0 + g * gstride) * cw * 4;
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                for (int s = 0; s < sp.ns; ++s) mn0 = fminf(mn0, col_filter(cg, e, na, x[4 * g + e], sp, s));
         }
     }
-    const float mn = fminf(mn0, mn1);
-    if (!(mn <= st.thr)) return;
-    // pass 2: candidates within 2 delta of the block minimum and under thr
+    return fminf(fminf(mn0, mn1), fminf(mn2, mn3));
+}
+
+// Pass 2, for a block whose minimum mn is <= st.thr: the candidates within
+// 2 delta of mn and under thr are re-scored exactly (groups are screened
+// with the packed filter, elements one by one).
+template <int NS, int NG>
+__device__ __forceinline__ void epi_pass2(RowState& st, const float (&x)[4 * NG], float mn,
+                                       const float* __restrict__ cf, int g0, int gstride,
+                                       int col_base, unsigned iso, float na, float delta,
+                                       float inv_n, int sr, const ColExact* __restrict__ ci,
+                                       int dn, const StepParams* __restrict__ spp)
+{
+    const StepParams& sp = *spp;
+    const int cw = (NS == 0) ? sp.cw : 1 + NS;
+
     float te = fminf(st.thr, __fadd_ru(mn, 2.0f * delta));
+    const int ns = (NS == 0) ? sp.ns : NS;
 #pragma unroll
-    for (int j = 0; j < NCOL; ++j) {
-        const float* cfc = cf + (size_t)(cf_col0 + j * cstride) * sp.cw;
-        float f[NSV];
-        const float m = filter_vals<NS>(cfc, a, x[j], sp, f);
-        if (m <= te) {
-            st = exact_col<NS>(st, x[j], cfc, col0 + j * cstride, iso, a, delta, inv_n, sr, ci,
+    for (int g = 0; g < NG; ++g) {
+        const float* cg = cf + (size_t)(g0 + g * gstride) * cw * 4;
+        const int col0 = (g0 + g * gstride) * 4 + col_base;
+        float gm = __int_as_float(0x7f800000);
+        if constexpr (NS >= 1 && NS <= 3) {
+            const uint64_t nak = pk2(na, na);
+            const float4 m = reinterpret_cast<const float4*>(cg)[0];
+            const uint64_t t01 = fma2(nak, pk2(m.x, m.y), pk2(x[4 * g], x[4 * g + 1]));
+            const uint64_t t23 = fma2(nak, pk2(m.z, m.w), pk2(x[4 * g + 2], x[4 * g + 3]));
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const float4 b = reinterpret_cast<const float4*>(cg)[1 + s];
+                const uint64_t nk = pk2(-sp.kf[s], -sp.kf[s]);
+                float f0, f1, f2, f3;
+                upk2(fma2(nk, t01, pk2(b.x, b.y)), f0, f1);
+                upk2(fma2(nk, t23, pk2(b.z, b.w)), f2, f3);
+                gm = fmin3(gm, f0, f1);
+                gm = fmin3(gm, f2, f3);
+            }
+        } else {
+            gm = -__int_as_float(0x7f800000);
+        }
+        if (!(gm <= te)) continue;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            float fm = __int_as_float(0x7f800000);
+            for (int s = 0; s < ns; ++s) fm = fminf(fm, col_filter(cg, e, na, x[4 * g + e], sp, s));
+            if (fm <= te) {
+                // Later columns of this row's sweep lose ties, so they win only
+                // with h <= h* - 1.  With this element's own error bound
+                // (4u (8pq|t'| + beta), twice the first-order bound; exactly 0
+                // for a flat domain) a lower bound f - err above (h* - 1)/n
+                // proves it cannot win.
+                if (st.h != kNoCandidate) {
+                    float lo = __int_as_float(0x7f800000);
+                    for (int s = 0; s < ns; ++s) {
+                        const float tp = __fmaf_rn(na, cg[e], x[4 * g + e]);
+                        const float beta = cg[(1 + s) * 4 + e];
+                        const float f = __fmaf_rn(-sp.kf[s], tp, beta);
+                        const float err = 0x1p-22f * __fmaf_ru(sp.kf[s], fabsf(tp), beta);
+                        lo = fminf(lo, __fsub_rd(f, err));
+                    }
+                    if (lo > __ll2float_ru(st.h - 1) * inv_n) continue;
+                }
+                st = exact_col(st, x[4 * g + e], cg, e, col0 + e, iso, na, delta, inv_n, sr, ci,
                                dn, spp, te);
-            te = fminf(te, st.thr);
+                te = fminf(te, st.thr);
+            }
         }
     }
+}
+
+// Pass 1 then, when the block can hold a winner, pass 2.
+template <int NS, int NG>
+__device__ __forceinline__ void epi_groups(RowState& st, const float (&x)[4 * NG],
+                                           const float* __restrict__ cf, int g0, int gstride,
+                                           int col_base, unsigned iso, float na, float delta,
+                                           float inv_n, int sr, const ColExact* __restrict__ ci,
+                                           int dn, const StepParams* __restrict__ spp)
+{
+    const float mn = epi_pass1<NS, NG>(x, cf, g0, gstride, na, spp);
+    if (mn <= st.thr)
+        epi_pass2<NS, NG>(st, x, mn, cf, g0, gstride, col_base, iso, na, delta, inv_n, sr, ci,
+                          dn, spp);
+}
+
+// Seed a row's threshold from the best exact key another column chunk has
+// published for it (any such key belongs to a real candidate, so it is >=
+// the row's true minimum and the seeded threshold still admits the argmin).
+__device__ __forceinline__ void row_state_seed(RowState& st, const long long* gbest, float inv_n,
+                                               float delta)
+{
+    const long long g = __ldcg(gbest);
+    if (g < kNoCandidate) st.thr = thr_from_h(g, inv_n, delta);
+}
+
+__device__ __forceinline__ void row_state_publish(const RowState& st, long long* gbest)
+{
+    if (st.h < kNoCandidate) atomicMin(gbest, st.h);
 }
 
 __device__ __forceinline__ void key_min_shfl(long long& h, unsigned& idx, int lane_mask)

@@ -25,6 +25,8 @@ struct ContractArgs {
     int ctiles_per_chunk; // column tiles per chunk (128 wide for the plain
                           // engine, 256 wide for the tensor engine)
     Best* part;           // R * n_chunks partial bests
+    long long* gbest;     // rows_pad best exact keys shared across column chunks
+                          // (filled with kNoCandidate before the launch)
     StepParams sp;
     int* err;             // device error word
     int grid_ctas;        // persistent grid size (tensor engine)
@@ -33,6 +35,7 @@ struct ContractArgs {
 cudaError_t launch_contract_plain(const ContractArgs& a, cudaStream_t s);
 cudaError_t launch_contract_tc(const ContractArgs& a, cudaStream_t s);
 size_t contract_tc_smem_bytes(int K);
+int contract_tc_parts_per_chunk();  // partial bests per (range, column chunk)
 
 // Step kernels (stages.cu).
 cudaError_t launch_entropy_table(double* T, int count, cudaStream_t s);
@@ -49,13 +52,15 @@ cudaError_t launch_pool_scatter(const uint32_t* flags, const uint32_t* pos, int6
 cudaError_t launch_gather(const uint8_t* img, int N, int B, int L, int per,
                           const uint32_t* pool_xy, int64_t dn, int64_t cols_pad, int K,
                           const StepParams& sp, __half* D, float* cf, ColExact* ci,
-                          unsigned long long* vd_max, cudaStream_t s);
+                          unsigned long long* vd_max, unsigned long long* vd_min_key,
+                          cudaStream_t s);
 cudaError_t launch_range_prep(const uint8_t* img, int N, int B, const uint32_t* act, int R,
                               int64_t rows_pad, int K, const StepParams& sp,
                               const unsigned long long* vd_max, __half* A, RowConst* rc,
                               cudaStream_t s);
 cudaError_t launch_split_decide(const Best* part, int n_chunks, const RowConst* rc, int R,
-                                int n, int q, int e16, int last, int dn, Best* best,
+                                int n, const StepParams& sp, int e16, int last, int dn,
+                                const unsigned long long* vd_min_key, Best* best,
                                 uint32_t* split, cudaStream_t s);
 cudaError_t launch_split_scatter(const uint32_t* act, const Best* best, const uint32_t* split,
                                  const uint32_t* split_pos, const RowConst* rc, int R, int B,

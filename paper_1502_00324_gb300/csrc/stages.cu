@@ -256,7 +256,8 @@ __global__ void __launch_bounds__(256)
 gather_kernel(const uint8_t* __restrict__ img, int N, int B, int L, int per,
               const uint32_t* __restrict__ pool_xy, int64_t dn, int64_t cols_pad,
               StepParams sp, __half* __restrict__ D, float* __restrict__ cf,
-              ColExact* __restrict__ ci, unsigned long long* __restrict__ vd_max)
+              ColExact* __restrict__ ci, unsigned long long* __restrict__ vd_max,
+              unsigned long long* __restrict__ vd_min_key)
 {
     constexpr int G = K / 8;
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -300,41 +301,46 @@ gather_kernel(const uint8_t* __restrict__ img, int N, int B, int L, int per,
         s2 += __shfl_xor_sync(0xffffffffu, s2, m);
     }
     if (kg != 0) return;
-    float* col = cf + c * sp.cw;
+    // constants in groups of 4 columns: constant j of column c at
+    // cf[((c / 4) * cw + j) * 4 + c % 4]
+    float* grp = cf + (c >> 2) * sp.cw * 4 + (c & 3);
     if (real) {
         const long long vd = (long long)n * s2 - (long long)s * s;
-        col[0] = (float)(s - kDomainCentre * n) * (1.0f / (float)n);
+        grp[0] = (float)(s - kDomainCentre * n) * (1.0f / (float)n);
         for (int t = 0; t < sp.ns; ++t)
-            col[1 + t] = __double2float_rn((double)sp.p[t] * sp.p[t] * (double)vd / (double)n);
+            grp[(1 + t) * 4] =
+                __double2float_rn((double)sp.p[t] * sp.p[t] * (double)vd / (double)n);
         ci[c] = ColExact{s, s2};
         atomicMax(vd_max, (unsigned long long)vd);
+        // (Vd << 24 | c): the smallest Vd, first index on ties (Vd < 2^36, c < 2^24)
+        atomicMin(vd_min_key, ((unsigned long long)vd << 24) | (unsigned long long)c);
     } else {
-        col[0] = 0.0f;
-        for (int t = 0; t < sp.ns; ++t) col[1 + t] = __int_as_float(0x7f800000);
+        grp[0] = 0.0f;
+        for (int t = 0; t < sp.ns; ++t) grp[(1 + t) * 4] = __int_as_float(0x7f800000);
         ci[c] = ColExact{0, 0};
     }
-    for (int t = 1 + sp.ns; t < sp.cw; ++t) col[t] = 0.0f;
 }
 
 cudaError_t launch_gather(const uint8_t* img, int N, int B, int L, int per,
                           const uint32_t* pool_xy, int64_t dn, int64_t cols_pad, int K,
                           const StepParams& sp, __half* D, float* cf, ColExact* ci,
-                          unsigned long long* vd_max, cudaStream_t s)
+                          unsigned long long* vd_max, unsigned long long* vd_min_key,
+                          cudaStream_t s)
 {
     const int64_t threads = cols_pad * (K / 8);
     const unsigned blocks = (unsigned)((threads + 255) / 256);
     switch (K) {
         case 16:
             gather_kernel<16><<<blocks, 256, 0, s>>>(img, N, B, L, per, pool_xy, dn, cols_pad,
-                                                     sp, D, cf, ci, vd_max);
+                                                     sp, D, cf, ci, vd_max, vd_min_key);
             break;
         case 64:
             gather_kernel<64><<<blocks, 256, 0, s>>>(img, N, B, L, per, pool_xy, dn, cols_pad,
-                                                     sp, D, cf, ci, vd_max);
+                                                     sp, D, cf, ci, vd_max, vd_min_key);
             break;
         case 256:
             gather_kernel<256><<<blocks, 256, 0, s>>>(img, N, B, L, per, pool_xy, dn, cols_pad,
-                                                      sp, D, cf, ci, vd_max);
+                                                      sp, D, cf, ci, vd_max, vd_min_key);
             break;
         default: return cudaErrorInvalidValue;
     }
@@ -431,38 +437,57 @@ cudaError_t launch_range_prep(const uint8_t* img, int N, int B, const uint32_t* 
 // score = 16 q^2 Vr + h.  The last step always stores its best mapping.
 // ---------------------------------------------------------------------------
 __global__ void split_decide_kernel(const Best* __restrict__ part, int n_chunks,
-                                    const RowConst* __restrict__ rc, int R, int n, int q,
-                                    int e16, int last, int dn, Best* __restrict__ best,
-                                    uint32_t* __restrict__ split)
+                                    const RowConst* __restrict__ rc, int R, int n, StepParams sp,
+                                    int e16, int last, int dn,
+                                    const unsigned long long* __restrict__ vd_min_key,
+                                    Best* __restrict__ best, uint32_t* __restrict__ split)
 {
     const int rho = blockIdx.x * blockDim.x + threadIdx.x;
     if (rho >= R) return;
+    const RowConst r = rc[rho];
     long long h = kNoCandidate;
     unsigned idx = 0xffffffffu;
-    for (int c = 0; c < n_chunks; ++c) {
-        const Best b = part[(int64_t)rho * n_chunks + c];
-        if (key_less(b.h, b.idx, h, idx)) {
-            h = b.h;
-            idx = b.idx;
+    if (dn > 0 && range_is_flat(r, n)) {
+        // h = p_s^2 Vd over all (c, k, s): k = 0; c = the first smallest-Vd
+        // domain, or c = 0 when p_s = 0 (then every domain gives h = 0)
+        const unsigned long long key = *vd_min_key;
+        const long long vdmin = (long long)(key >> 24);
+        const unsigned cmin = (unsigned)(key & 0xffffffu);
+        for (int s = 0; s < sp.ns; ++s) {
+            const long long ps = sp.p[s];
+            const long long hs = ps == 0 ? 0 : ps * ps * vdmin;
+            const unsigned is = pack_idx(ps == 0 ? 0u : cmin, 0u, (unsigned)s);
+            if (key_less(hs, is, h, idx)) {
+                h = hs;
+                idx = is;
+            }
+        }
+    } else {
+        for (int c = 0; c < n_chunks; ++c) {
+            const Best b = part[(int64_t)rho * n_chunks + c];
+            if (key_less(b.h, b.idx, h, idx)) {
+                h = b.h;
+                idx = b.idx;
+            }
         }
     }
-    bool sp;
+    const int q = sp.q;
+    bool sp_;
     if (dn == 0 || h == kNoCandidate) {
-        sp = !last;
+        sp_ = !last;
     } else {
-        const RowConst r = rc[rho];
         const long long vr = (long long)n * r.sr2 - (long long)r.sr * r.sr;
         const long long qq = (long long)q * q;
         const long long score = 16LL * qq * vr + h;
         const long long lim = 16LL * qq * n * n * (long long)e16 * e16;
-        sp = !last && 256LL * score > lim;
+        sp_ = !last && 256LL * score > lim;
     }
     Best b;
     b.h = h;
     b.idx = idx;
     b.pad = 0;
     best[rho] = b;
-    split[rho] = sp ? 1u : 0u;
+    split[rho] = sp_ ? 1u : 0u;
 }
 
 __global__ void split_scatter_kernel(const uint32_t* __restrict__ act, const Best* __restrict__ best,
@@ -518,12 +543,13 @@ __global__ void split_scatter_kernel(const uint32_t* __restrict__ act, const Bes
 }
 
 cudaError_t launch_split_decide(const Best* part, int n_chunks, const RowConst* rc, int R,
-                                int n, int q, int e16, int last, int dn, Best* best,
+                                int n, const StepParams& sp, int e16, int last, int dn,
+                                const unsigned long long* vd_min_key, Best* best,
                                 uint32_t* split, cudaStream_t s)
 {
     if (R == 0) return cudaSuccess;
-    split_decide_kernel<<<(R + 255) / 256, 256, 0, s>>>(part, n_chunks, rc, R, n, q, e16, last,
-                                                        dn, best, split);
+    split_decide_kernel<<<(R + 255) / 256, 256, 0, s>>>(part, n_chunks, rc, R, n, sp, e16, last,
+                                                        dn, vd_min_key, best, split);
     return cudaGetLastError();
 }
 

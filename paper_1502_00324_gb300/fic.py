@@ -69,13 +69,16 @@ assert CODE_DTYPE.itemsize == C.sizeof(FicCode) == 16
 
 EXPORTS = ["fic_encode", "fic_encode_ex", "fic_decode", "fic_domain_pool", "fic_result_free",
            "fic_strerror", "fic_stats_reset", "fic_stats_read", "fic_version",
-           "fic_domain_pool_noalloc"]
+           "fic_domain_pool_noalloc", "fic_last_error"]
 
 
 class FicError(RuntimeError):
     def __init__(self, status, what=""):
         self.status = status
-        super().__init__(f"{what}: {strerror(status)} ({status})")
+        detail = ""
+        if status in (FIC_ECUDA, FIC_ENOMEM):
+            detail = " [" + lib().fic_last_error().decode() + "]"
+        super().__init__(f"{what}: {strerror(status)} ({status}){detail}")
 
 
 _lib = None
@@ -104,6 +107,7 @@ def lib():
     L.fic_stats_reset.argtypes = [C.c_int]
     L.fic_stats_read.argtypes = [C.POINTER(FicStats)]
     L.fic_version.restype = C.c_char_p
+    L.fic_last_error.restype = C.c_char_p
     L.fic_domain_pool_noalloc.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_double, vp,
                                           C.c_int64, C.POINTER(C.c_int64), vp,
                                           C.POINTER(C.c_int64), vp]
