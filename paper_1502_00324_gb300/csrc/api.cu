@@ -136,7 +136,7 @@ struct Context {
     bool ready = false;
     int sm_count = 0;
     DevBuf img, entT, flags, pos, scan_tmp, pool, D, cf, ci, A, rc, part, best, split,
-        split_pos, act0, act1, codes_tmp, codes_out, cellmap, cellflag, cellrank, H, gbest,
+        split_pos, act0, act1, codes_tmp, codes_out, cellmap, cellflag, cellrank, H, gbest, box2,
         dec0, dec1, scal;
     Scalars* host_scal = nullptr;  // pinned
     static constexpr int kEntTable = 4097;
@@ -303,12 +303,8 @@ int build_pool(Context* c, Launcher& L, const uint8_t* dimg, int N, int B, int L
 // chunk of column tiles).  Picks the chunk count that minimises the
 // estimated makespan over `slots` concurrent items (waves x tiles per item,
 // plus a per-item cost of refilling the pipeline).
-void choose_chunks(int engine, int sm_count, int64_t rows_pad, int64_t cols_pad, int* n_chunks,
-                   int* per_chunk)
+void choose_chunks(int sm_count, int64_t n_mtiles, int64_t n_ct, int* n_chunks, int* per_chunk)
 {
-    const int64_t n_mtiles = rows_pad / kMTile;
-    const int64_t tile_w = engine == FIC_ENGINE_TENSOR ? kNTile : 128;
-    const int64_t n_ct = cols_pad / tile_w;
     const int64_t slots = sm_count;
     const double item_cost = 2.0;  // in tiles
     int64_t best_nc = 1;
@@ -361,6 +357,12 @@ int encode_impl(const uint8_t* img, const fic_params* p, fic_code* codes_out, in
         dimg = c->img.as<uint8_t>();
     }
 
+    // 2x2 box sums, shared by every step's domain gather
+    FIC_TRY(c->box2.ensure(sizeof(uint16_t) * (size_t)N * N));
+    L.begin(FIC_K_GATHER);
+    FIC_TRY(launch_box2(dimg, N, c->box2.as<uint16_t>(), s));
+    L.end(1, 0.0, (double)N * N * 3.0);
+
     // capacity of records and cells: every record covers >= 1 finest cell
     const int64_t cells = (int64_t)(N / p->B_min) * (N / p->B_min);
     FIC_TRY(c->codes_tmp.ensure(sizeof(fic_code) * cells));
@@ -404,8 +406,12 @@ int encode_impl(const uint8_t* img, const fic_params* p, fic_code* codes_out, in
         const uint32_t* pool_xy = use_list ? c->pool.as<uint32_t>() : nullptr;
 
         const StepParams sp = make_step(p->S_sets[lvl], n);
-        const int64_t cols_pad = round_up(dn > 0 ? dn : 1, kNTile);
-        const int64_t rows_pad = round_up(8 * R, kMTile);
+        const int64_t cols_pad = round_up(dn > 0 ? dn : 1, kColPad);
+        // 2x2 .. 8x8 ranges with up to 3 S values: isometry-in-accumulator
+        // kernel (ranges in TMEM lanes, iso-major A); otherwise rows are
+        // (range, isometry) pairs
+        const bool iso = p->engine == FIC_ENGINE_TENSOR && contract_tc_iso_supports(K, sp.ns);
+        const int64_t rows_pad = iso ? 8 * round_up(R, 128) : round_up(8 * R, kMTile);
 
         FIC_TRY(c->D.ensure(sizeof(__half) * cols_pad * K));
         FIC_TRY(c->cf.ensure(sizeof(float) * cols_pad * sp.cw));
@@ -420,23 +426,27 @@ int encode_impl(const uint8_t* img, const fic_params* p, fic_code* codes_out, in
         FIC_TRY(cudaMemsetAsync(&ds->vd_max, 0, sizeof(unsigned long long), s));
         FIC_TRY(cudaMemsetAsync(&ds->vd_min_key, 0xff, sizeof(unsigned long long), s));
         L.begin(FIC_K_GATHER);
-        FIC_TRY(launch_gather(dimg, N, B, Lstep, per, pool_xy, dn, cols_pad, K, sp,
+        FIC_TRY(launch_gather(c->box2.as<uint16_t>(), N, B, Lstep, per, pool_xy, dn, cols_pad, K, sp,
                               c->D.as<__half>(), c->cf.as<float>(), c->ci.as<ColExact>(),
                               &ds->vd_max, &ds->vd_min_key, s));
         L.end(1, 0.0, (double)cols_pad * (2.0 * K + 4.0 * sp.cw + 8.0) + (double)dn * 4.0 * n);
 
         L.begin(FIC_K_RANGE_PREP);
-        FIC_TRY(launch_range_prep(dimg, N, B, act, (int)R, rows_pad, K, sp, &ds->vd_max,
+        FIC_TRY(launch_range_prep(dimg, N, B, act, (int)R, rows_pad, K, sp, &ds->vd_max, iso ? 1 : 0,
                                   c->A.as<__half>(), c->rc.as<RowConst>(), s));
         L.end(1, 0.0, (double)rows_pad * K * 2.0 + (double)R * (n + 20.0));
 
         int n_chunks = 0, n_parts = 0;
         if (dn > 0) {
             int per_chunk = 0;
-            choose_chunks(p->engine, c->sm_count, rows_pad, cols_pad, &n_chunks, &per_chunk);
-            // the tensor engine writes one partial per chunk and column slice
-            n_parts = p->engine == FIC_ENGINE_TENSOR ? contract_tc_parts_per_chunk() * n_chunks
-                                                     : n_chunks;
+            const int64_t tile_w = iso ? contract_tc_iso_ntile(K)
+                                       : (p->engine == FIC_ENGINE_TENSOR ? contract_tc_ntile() : 128);
+            const int64_t n_mtiles = iso ? rows_pad / 8 / 128 : rows_pad / kMTile;
+            choose_chunks(c->sm_count, n_mtiles, cols_pad / tile_w, &n_chunks, &per_chunk);
+            // the tensor kernels write one partial per chunk and column slice
+            n_parts = iso ? contract_tc_iso_parts_per_chunk() * n_chunks
+                          : (p->engine == FIC_ENGINE_TENSOR ? contract_tc_parts_per_chunk() * n_chunks
+                                                            : n_chunks);
             FIC_TRY(c->part.ensure(sizeof(Best) * R * n_parts));
             FIC_TRY(c->gbest.ensure(sizeof(long long) * rows_pad));
             FIC_TRY(cudaMemsetAsync(c->gbest.p, 0x7f, sizeof(long long) * rows_pad, s));
@@ -464,7 +474,7 @@ int encode_impl(const uint8_t* img, const fic_params* p, fic_code* codes_out, in
             if (p->engine == FIC_ENGINE_TENSOR) {
                 FIC_TRY(cudaMemsetAsync(&ds->err, 0, sizeof(int), s));
                 L.begin(FIC_K_CONTRACT_TC);
-                FIC_TRY(launch_contract_tc(a, s));
+                FIC_TRY(iso ? launch_contract_tc_iso(a, s) : launch_contract_tc(a, s));
                 L.end(1, flops, bytes, matches);
             } else {
                 L.begin(FIC_K_CONTRACT_PLAIN);

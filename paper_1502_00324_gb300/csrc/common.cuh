@@ -49,10 +49,11 @@ __host__ __device__ inline int64_t tile_off(int64_t row, int k, int64_t rows_pad
 }
 
 // Tiles: the M tile is 128 rows = 16 ranges x 8 isometries (row = 8 range +
-// isometry, so each range is one 8-row group); the N tile is 256 domains.
+// isometry, so each range is one 8-row group).  The pool is padded to a
+// multiple of kColPad so that any N tile of 128, 192 or 256 columns divides it.
 constexpr int kMTile = 128;
 constexpr int kRangesPerTile = kMTile / 8;
-constexpr int kNTile = 256;
+constexpr int kColPad = 768;
 
 // ---------------------------------------------------------------------------
 // Per-range and per-domain constants.

@@ -31,173 +31,25 @@
 
 #include "epilogue.cuh"
 #include "kernels.h"
+#include "tc_common.cuh"
 
 namespace fic {
 namespace {
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-constexpr long long kWaitCycles = 8000000000LL;   // ~4 s at 2 GHz: far above any stage wait
-constexpr long long kDrainCycles = 400000000LL;   // ~0.2 s for the drain after an error
-
-// Bounded parity wait.  try_wait suspends the thread in hardware between
-// polls; the cycle counter and the error word are only looked at every 256
-// unsuccessful polls.  Returns false when the limit passed or another
-// thread already recorded an error.
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, long long limit)
-{
-    long long t0 = 0;
-    for (uint32_t i = 1;; ++i) {
-        if (mbar_try(bar, parity)) return true;
-        if ((i & 255) == 0) {
-            if (*(volatile int*)err) return false;
-            const long long now = clock64();
-            if (t0 == 0) {
-                t0 = now;
-            } else if (now - t0 > limit) {
-                atomicCAS(err, 0, kErrTimeout);
-                return false;
-            }
-        }
-    }
-}
-
-// Bulk async copy global -> shared (the TMA engine, non-tensor form),
-// completing on an mbarrier.  Addresses 16-byte aligned, size % 16 == 0.
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
-                                         uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-        ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before()
-{
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after()
-{
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_commit(uint32_t bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                 ::"r"(bar)
-                 : "memory");
-}
-
-// D[tmem] (+)= A[smem] . B[smem]^T, M = 128, N = 256, K = 16.
-__device__ __forceinline__ void tc_mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                           uint32_t idesc, uint32_t accumulate)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
-        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-// 32 lanes x 64 consecutive FP32 columns; thread i gets lane (base lane + i).
-__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64])
-{
-    uint32_t r[64];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
-        : "r"(taddr));
-    // the wait takes the registers as operands so no use moves above it
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31]), "+r"(r[32]), "+r"(r[33]), "+r"(r[34]), "+r"(r[35]), "+r"(r[36]), "+r"(r[37]), "+r"(r[38]), "+r"(r[39]), "+r"(r[40]), "+r"(r[41]), "+r"(r[42]), "+r"(r[43]), "+r"(r[44]), "+r"(r[45]), "+r"(r[46]), "+r"(r[47]), "+r"(r[48]), "+r"(r[49]), "+r"(r[50]), "+r"(r[51]), "+r"(r[52]), "+r"(r[53]), "+r"(r[54]), "+r"(r[55]), "+r"(r[56]), "+r"(r[57]), "+r"(r[58]), "+r"(r[59]), "+r"(r[60]), "+r"(r[61]), "+r"(r[62]), "+r"(r[63])
-                 :
-                 : "memory");
-#pragma unroll
-    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// 32 lanes x 32 consecutive FP32 columns, issued without waiting: the
-// registers of v are written asynchronously and may be read only after
-// tmem_wait32(v).
-__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, float (&v)[32])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]), "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15]), "=f"(v[16]), "=f"(v[17]), "=f"(v[18]), "=f"(v[19]), "=f"(v[20]), "=f"(v[21]), "=f"(v[22]), "=f"(v[23]), "=f"(v[24]), "=f"(v[25]), "=f"(v[26]), "=f"(v[27]), "=f"(v[28]), "=f"(v[29]), "=f"(v[30]), "=f"(v[31])
-        : "r"(taddr));
-}
-
-// Waits for this thread's outstanding tcgen05.ld; v is an operand so that no
-// use of it moves above the wait.
-__device__ __forceinline__ void tmem_wait32(float (&v)[32])
-{
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]), "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]), "+f"(v[13]), "+f"(v[14]), "+f"(v[15]), "+f"(v[16]), "+f"(v[17]), "+f"(v[18]), "+f"(v[19]), "+f"(v[20]), "+f"(v[21]), "+f"(v[22]), "+f"(v[23]), "+f"(v[24]), "+f"(v[25]), "+f"(v[26]), "+f"(v[27]), "+f"(v[28]), "+f"(v[29]), "+f"(v[30]), "+f"(v[31])
-                 :
-                 : "memory");
-}
-
-// Shared-memory matrix descriptor, K-major, no swizzle: start address,
-// leading (K-direction core matrix) and stride (8-row group) byte offsets,
-// descriptor version 1 at bits 46-47.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
-{
-    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-
-// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = F16,
-// both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-__host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N)
-{
-    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
+using namespace tc;
 
 #ifndef FIC_TC_EPI_WARPS
 #define FIC_TC_EPI_WARPS 8
 #endif
+#ifndef FIC_TC_NTILE
+#define FIC_TC_NTILE 256
+#endif
 #ifndef FIC_TC_PIPE
 #define FIC_TC_PIPE 0
 #endif
-constexpr int kEpiWarps = FIC_TC_EPI_WARPS;     // epilogue warps, 4 per lane quadrant group
+constexpr int kEpiWarps = FIC_TC_EPI_WARPS;     // epilogue warps, a multiple of 4
+constexpr int kN = FIC_TC_NTILE;                // MMA N = pool columns per tile
 constexpr int kThreads = 32 * (2 + kEpiWarps);
-constexpr int kColsPerEpiWarp = 256 * 4 / kEpiWarps;
+constexpr int kColsPerEpiWarp = kN * 4 / kEpiWarps;
 constexpr int kEpiBlocks = kColsPerEpiWarp / 32;      // 32-column blocks per tile
 constexpr int kPartsPerChunk = kEpiWarps / 4;         // partials per (range, column chunk)
 // Registers live in four 16K-entry files, one per SM sub-partition, and the
@@ -228,10 +80,10 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
     constexpr int KB = K < 64 ? K : 64;
     constexpr int NKB = K / KB;
     constexpr uint32_t kAKBBytes = 128u * KB * 2u;     // one K-block of the A tile
-    constexpr uint32_t kBStageBytes = 256u * KB * 2u;  // one K-block of a D tile
+    constexpr uint32_t kBStageBytes = (uint32_t)kN * KB * 2u;  // one K-block of a D tile
     constexpr uint32_t kSbo = KB * 16u;                // 8-row group stride
-    constexpr uint32_t kIdesc = idesc_f16_f32(128, 256);
-    const uint32_t cf_bytes = 256u * (uint32_t)sp.cw * 4u;
+    constexpr uint32_t kIdesc = idesc_f16_f32(128, kN);
+    const uint32_t cf_bytes = (uint32_t)kN * (uint32_t)sp.cw * 4u;
     const int nstage = P.nstage;
     const int ncf = P.ncf;  // column-constant tiles in flight (ring)
 
@@ -287,94 +139,107 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
 
     if (warp == 0) {
         // ------------------------------------------------------------ producer
-        if (lane == 0) {
-            int64_t it = 0, tcount = 0, icount = 0;
-            bool ok = true;
-            for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
-                const int chunk = item / P.n_mtiles, mtile = item % P.n_mtiles;
-                const int ct0 = chunk * P.per_chunk;
-                const int ct1 = min(P.n_ct, ct0 + P.per_chunk);
-                if (!(ok = mbar_wait(a_empty, (uint32_t)((icount & 1) ^ 1), err, kWaitCycles))) break;
+        // the whole warp walks the schedule; one elected lane issues copies
+        int64_t it = 0, tcount = 0, cfi = 0, icount = 0;
+        bool ok = true;
+        for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
+            const int chunk = item / P.n_mtiles, mtile = item % P.n_mtiles;
+            const int ct0 = chunk * P.per_chunk;
+            const int ct1 = min(P.n_ct, ct0 + P.per_chunk);
+            if (!(ok = mbar_wait_warp(a_empty, (uint32_t)((icount & 1) ^ 1), err, kWaitCycles))) break;
+            if (elect_one()) {
                 mbar_expect_tx(a_full, NKB * kAKBBytes);
                 for (int kb = 0; kb < NKB; ++kb)
                     bulk_g2s(smem_u32(sA + kb * kAKBBytes),
                              P.A + ((int64_t)kb * P.rows_pad * KB + (int64_t)mtile * 128 * KB),
                              kAKBBytes, a_full);
-                ++icount;
-                for (int ct = ct0; ct < ct1 && ok; ++ct) {
-                    const int cb = (int)(tcount % ncf);
-                    const uint32_t cph = (uint32_t)((tcount / ncf) & 1);
-                    if (!(ok = mbar_wait(cfe(cb), cph ^ 1, err, kWaitCycles))) break;
+            }
+            __syncwarp();
+            ++icount;
+            for (int ct = ct0; ct < ct1 && ok; ++ct) {
+                const int cb = (int)(tcount % ncf);
+                const uint32_t cph = (uint32_t)((tcount / ncf) & 1);
+                if (!(ok = mbar_wait_warp(cfe(cb), cph ^ 1, err, kWaitCycles))) break;
+                if (elect_one()) {
                     mbar_expect_tx(cff(cb), cf_bytes);
-                    bulk_g2s(smem_u32(sCF + (size_t)cb * cf_bytes), P.cf + (int64_t)ct * 256 * sp.cw,
+                    bulk_g2s(smem_u32(sCF + (size_t)cb * cf_bytes), P.cf + (int64_t)ct * kN * sp.cw,
                              cf_bytes, cff(cb));
-                    for (int kb = 0; kb < NKB; ++kb) {
-                        const int s = (int)(it % nstage);
-                        const uint32_t sph = (uint32_t)((it / nstage) & 1);
-                        if (!(ok = mbar_wait(empty(s), sph ^ 1, err, kWaitCycles))) break;
+                }
+                __syncwarp();
+                ++cfi;
+                for (int kb = 0; kb < NKB; ++kb) {
+                    const int s = (int)(it % nstage);
+                    const uint32_t sph = (uint32_t)((it / nstage) & 1);
+                    if (!(ok = mbar_wait_warp(empty(s), sph ^ 1, err, kWaitCycles))) break;
+                    if (elect_one()) {
                         mbar_expect_tx(full(s), kBStageBytes);
                         bulk_g2s(smem_u32(sB + (size_t)s * kBStageBytes),
-                                 P.D + ((int64_t)kb * P.cols_pad * KB + (int64_t)ct * 256 * KB),
+                                 P.D + ((int64_t)kb * P.cols_pad * KB + (int64_t)ct * kN * KB),
                                  kBStageBytes, full(s));
-                        ++it;
                     }
-                    ++tcount;
+                    __syncwarp();
+                    ++it;
                 }
+                ++tcount;
             }
-            if (!ok) {
-                // drain: let every copy this thread armed land before exit
-                for (int64_t j = (it > nstage ? it - nstage : 0); j < it; ++j)
-                    mbar_wait(full((int)(j % nstage)), (uint32_t)((j / nstage) & 1), err + 1,
-                              kDrainCycles);
-                if (icount > 0) mbar_wait(a_full, (uint32_t)((icount - 1) & 1), err + 1, kDrainCycles);
-                for (int64_t j = (tcount > ncf ? tcount - ncf : 0); j < tcount; ++j)
-                    mbar_wait(cff((int)(j % ncf)), (uint32_t)((j / ncf) & 1), err + 1, kDrainCycles);
-            }
+        }
+        if (!ok && lane == 0) {
+            // drain: let every copy this warp armed land before exit
+            for (int64_t j = (it > nstage ? it - nstage : 0); j < it; ++j)
+                mbar_wait(full((int)(j % nstage)), (uint32_t)((j / nstage) & 1), err + 1,
+                          kDrainCycles);
+            if (icount > 0) mbar_wait(a_full, (uint32_t)((icount - 1) & 1), err + 1, kDrainCycles);
+            for (int64_t j = (cfi > ncf ? cfi - ncf : 0); j < cfi; ++j)
+                mbar_wait(cff((int)(j % ncf)), (uint32_t)((j / ncf) & 1), err + 1, kDrainCycles);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
-        if (lane == 0) {
-            int64_t it = 0, tcount = 0, icount = 0;
-            bool ok = true;
-            for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
-                const int chunk = item / P.n_mtiles;
-                const int ct0 = chunk * P.per_chunk;
-                const int ct1 = min(P.n_ct, ct0 + P.per_chunk);
-                if (!(ok = mbar_wait(a_full, (uint32_t)(icount & 1), err, kWaitCycles))) break;
+        const uint64_t a_desc = smem_desc(smem_u32(sA), 128u, kSbo);
+        int64_t it = 0, tcount = 0, icount = 0;
+        bool ok = true;
+        for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
+            const int chunk = item / P.n_mtiles;
+            const int ct0 = chunk * P.per_chunk;
+            const int ct1 = min(P.n_ct, ct0 + P.per_chunk);
+            if (!(ok = mbar_wait_warp(a_full, (uint32_t)(icount & 1), err, kWaitCycles))) break;
+            tc_fence_after();
+            for (int ct = ct0; ct < ct1 && ok; ++ct) {
+                const int acc = (int)(tcount & 1);
+                const uint32_t ph = (uint32_t)((tcount >> 1) & 1);
+                if (!(ok = mbar_wait_warp(tempty(acc), ph ^ 1, err, kWaitCycles))) break;
                 tc_fence_after();
-                for (int ct = ct0; ct < ct1 && ok; ++ct) {
-                    const int acc = (int)(tcount & 1);
-                    const uint32_t ph = (uint32_t)((tcount >> 1) & 1);
-                    if (!(ok = mbar_wait(tempty(acc), ph ^ 1, err, kWaitCycles))) break;
+                const uint32_t d_tmem = tmem_base + (uint32_t)acc * 256u;  // 256-column slots
+                for (int kb = 0; kb < NKB; ++kb) {
+                    const int s = (int)(it % nstage);
+                    const uint32_t sph = (uint32_t)((it / nstage) & 1);
+                    if (!(ok = mbar_wait_warp(full(s), sph, err, kWaitCycles))) break;
                     tc_fence_after();
-                    const uint32_t d_tmem = tmem_base + (uint32_t)acc * 256u;
-                    for (int kb = 0; kb < NKB; ++kb) {
-                        const int s = (int)(it % nstage);
-                        const uint32_t sph = (uint32_t)((it / nstage) & 1);
-                        if (!(ok = mbar_wait(full(s), sph, err, kWaitCycles))) break;
-                        tc_fence_after();
-                        const uint32_t a0 = smem_u32(sA + kb * kAKBBytes);
-                        const uint32_t b0 = smem_u32(sB + (size_t)s * kBStageBytes);
+                    const uint64_t ak = desc_add(a_desc, (uint32_t)kb * kAKBBytes);
+                    const uint64_t bk = smem_desc(smem_u32(sB + (size_t)s * kBStageBytes), 128u, kSbo);
+                    if (elect_one()) {
 #pragma unroll
                         for (int j = 0; j < KB / 16; ++j)
-                            tc_mma_f16(d_tmem, smem_desc(a0 + 256u * j, 128u, kSbo),
-                                       smem_desc(b0 + 256u * j, 128u, kSbo), kIdesc,
+                            tc_mma_f16(d_tmem, desc_add(ak, 256u * j), desc_add(bk, 256u * j), kIdesc,
                                        (kb | j) != 0 ? 1u : 0u);
                         tc_commit(empty(s));
-                        ++it;
                     }
-                    if (!ok) break;
-                    tc_commit(tfull(acc));
-                    ++tcount;
+                    __syncwarp();
+                    ++it;
                 }
                 if (!ok) break;
-                tc_commit(a_empty);
-                ++icount;
+                if (elect_one()) tc_commit(tfull(acc));
+                __syncwarp();
+                ++tcount;
             }
-            // every issued MMA has finished before TMEM is released
-            tc_commit(drain);
-            mbar_wait(drain, 0, err + 1, kWaitCycles);
+            if (!ok) break;
+            if (elect_one()) tc_commit(a_empty);
+            __syncwarp();
+            ++icount;
         }
+        // every issued MMA has finished before TMEM is released
+        if (elect_one()) tc_commit(drain);
+        __syncwarp();
+        mbar_wait(drain, 0, err + 1, kWaitCycles);
     } else {
         // ------------------------------------------------------------ epilogue
         const int e = warp - 2;
@@ -406,7 +271,7 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
                 tc_fence_after();
                 const float* cfs = reinterpret_cast<const float*>(sCF + (size_t)cb * cf_bytes);
                 const uint32_t tb = tmem_base + ((uint32_t)(quad * 32) << 16) +
-                                    (uint32_t)(acc * 256 + cq * kColsPerEpiWarp);
+                                    (uint32_t)(acc * 256 + cq * kColsPerEpiWarp);  // 256-column slots
 #if FIC_TC_PIPE
                 // double-buffered 32-column loads: block b+1 streams in while
                 // pass 1 scores block b; the wait comes before the (rare) pass 2
@@ -437,7 +302,7 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
                         tmem_wait32(nxt);
                     }
                     if (mn <= st.thr)
-                        epi_pass2<NS, 8>(st, cur, mn, cfs, g0, 1, ct * 256, iso, -r.a, r.delta,
+                        epi_pass2<NS, 8>(st, cur, mn, cfs, g0, 1, ct * kN, iso, -r.a, r.delta,
                                          inv_n, r.sr, P.ci, P.dn, &sp);
                 }
 #else
@@ -455,7 +320,7 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
                     }
                     if (valid)
                         epi_groups<NS, 8>(st, x, cfs, (cq * kColsPerEpiWarp + 32 * b) / 4, 1,
-                                          ct * 256, iso, -r.a, r.delta, inv_n, r.sr, P.ci, P.dn,
+                                          ct * kN, iso, -r.a, r.delta, inv_n, r.sr, P.ci, P.dn,
                                           &sp);
                 }
 #endif
@@ -500,8 +365,8 @@ size_t tc_layout(int cw, int* nstage_out, int* ncf_out)
 {
     constexpr int KB = K < 64 ? K : 64;
     const size_t a_bytes = (size_t)128 * K * 2;
-    const size_t stage = (size_t)256 * KB * 2;
-    const size_t cf_tile = (size_t)256 * cw * 4;
+    const size_t stage = (size_t)kN * KB * 2;
+    const size_t cf_tile = (size_t)kN * cw * 4;
     const int ncf = cf_tile <= 4096 ? 8 : 2;  // deep ring for the usual 1-3 S values
     const size_t fixed = a_bytes + (size_t)ncf * cf_tile + 1024;
     int ns = (int)((kSmemBudget - fixed) / stage);
@@ -538,7 +403,7 @@ cudaError_t launch_tc_kns(const ContractArgs& a, cudaStream_t s)
     P.dn = a.dn;
     P.n_chunks = a.n_chunks;
     P.per_chunk = a.ctiles_per_chunk;
-    P.n_ct = (int)(a.cols_pad / 256);
+    P.n_ct = (int)(a.cols_pad / kN);
     P.n_mtiles = (int)(a.rows_pad / 128);
     P.n_items = P.n_mtiles * a.n_chunks;
     P.nstage = nstage;
@@ -572,6 +437,7 @@ cudaError_t launch_contract_tc(const ContractArgs& a, cudaStream_t s)
 }
 
 int contract_tc_parts_per_chunk() { return kPartsPerChunk; }
+int contract_tc_ntile() { return kN; }
 
 size_t contract_tc_smem_bytes(int K)
 {

@@ -14,7 +14,7 @@ struct ContractArgs {
     const __half* A;      // ranges x isometries, tile layout, rows_pad rows
     int64_t rows_pad;     // multiple of 128
     const __half* D;      // pool domains, tile layout, cols_pad rows
-    int64_t cols_pad;     // multiple of 256
+    int64_t cols_pad;     // multiple of kColPad (768)
     int K;                // 16, 64 or 256
     const float* cf;      // column filter constants, cols_pad * sp.cw floats
     const ColExact* ci;   // exact column sums, cols_pad entries
@@ -34,8 +34,16 @@ struct ContractArgs {
 
 cudaError_t launch_contract_plain(const ContractArgs& a, cudaStream_t s);
 cudaError_t launch_contract_tc(const ContractArgs& a, cudaStream_t s);
+// Isometry-in-accumulator tensor kernel (K = 16 or 64, |S| <= 3); A in the
+// iso-major layout (rows k * Rpad + range, Rpad = rows_pad / 8, a multiple
+// of 128); partials per range; gbest per range.
+cudaError_t launch_contract_tc_iso(const ContractArgs& a, cudaStream_t s);
+bool contract_tc_iso_supports(int K, int ns);
+int contract_tc_iso_parts_per_chunk();
+int contract_tc_iso_ntile(int K);
 size_t contract_tc_smem_bytes(int K);
 int contract_tc_parts_per_chunk();  // partial bests per (range, column chunk)
+int contract_tc_ntile();            // pool columns per tensor-core tile
 
 // Step kernels (stages.cu).
 cudaError_t launch_entropy_table(double* T, int count, cudaStream_t s);
@@ -49,15 +57,18 @@ cudaError_t launch_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* 
                         uint32_t* total, cudaStream_t s, int* launches);
 cudaError_t launch_pool_scatter(const uint32_t* flags, const uint32_t* pos, int64_t n_pos,
                                 int per, int L, uint32_t* pool_xy, cudaStream_t s);
-cudaError_t launch_gather(const uint8_t* img, int N, int B, int L, int per,
+// 2x2 box sums of the image, pitch N (entries with x or y = N - 1 unused).
+cudaError_t launch_box2(const uint8_t* img, int N, uint16_t* s2, cudaStream_t s);
+cudaError_t launch_gather(const uint16_t* s2img, int N, int B, int L, int per,
                           const uint32_t* pool_xy, int64_t dn, int64_t cols_pad, int K,
                           const StepParams& sp, __half* D, float* cf, ColExact* ci,
                           unsigned long long* vd_max, unsigned long long* vd_min_key,
                           cudaStream_t s);
+// iso_major = 0: row 8 range + k; 1: row k * (rows_pad / 8) + range.
 cudaError_t launch_range_prep(const uint8_t* img, int N, int B, const uint32_t* act, int R,
                               int64_t rows_pad, int K, const StepParams& sp,
-                              const unsigned long long* vd_max, __half* A, RowConst* rc,
-                              cudaStream_t s);
+                              const unsigned long long* vd_max, int iso_major, __half* A,
+                              RowConst* rc, cudaStream_t s);
 cudaError_t launch_split_decide(const Best* part, int n_chunks, const RowConst* rc, int R,
                                 int n, const StepParams& sp, int e16, int last, int dn,
                                 const unsigned long long* vd_min_key, Best* best,

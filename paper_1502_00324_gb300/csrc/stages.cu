@@ -246,18 +246,39 @@ cudaError_t launch_pool_scatter(const uint32_t* flags, const uint32_t* pos, int6
 }
 
 // ---------------------------------------------------------------------------
+// 2x2 box sums S2[y][x] = img[y][x] + img[y][x+1] + img[y+1][x] + img[y+1][x+1]
+// (pitch N, x, y < N - 1): the decimated value d' of every domain at every
+// step is one S2 entry, so the image is summed once per encode.
+// ---------------------------------------------------------------------------
+__global__ void box2_kernel(const uint8_t* __restrict__ img, int N, uint16_t* __restrict__ s2)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= N - 1 || y >= N - 1) return;
+    const uint8_t* p0 = img + (int64_t)y * N + x;
+    s2[(int64_t)y * N + x] = (uint16_t)((int)p0[0] + p0[1] + p0[N] + p0[N + 1]);
+}
+
+cudaError_t launch_box2(const uint8_t* img, int N, uint16_t* s2, cudaStream_t s)
+{
+    if (N < 2) return cudaSuccess;
+    dim3 grid((unsigned)((N - 1 + 255) / 256), (unsigned)(N - 1));
+    box2_kernel<<<grid, 256, 0, s>>>(img, N, s2);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Domain gather (Sec. 2 decimation): for pool column c, the B x B array of
-// 2x2 sums d' is written centred (d' - 510, FP16, exact) into the tile
-// layout, with sum d', sum d'^2 and the filter constants m_c, beta_s.
-// K/8 threads per column, each producing one 16-byte row of a core matrix.
+// 2x2 sums d' (d'[i][j] = S2[y + 2i][x + 2j]) is written centred (d' - 510,
+// FP16, exact) into the tile layout, with sum d', sum d'^2 and the filter
+// constants m_c, beta_s.  K/8 threads per column, each producing one 16-byte
+// row of a core matrix.
 // ---------------------------------------------------------------------------
 template <int K>
 __global__ void __launch_bounds__(256)
-gather_kernel(const uint8_t* __restrict__ img, int N, int B, int L, int per,
+gather_kernel(const uint16_t* __restrict__ box, int N, int B, int L, int per,
               const uint32_t* __restrict__ pool_xy, int64_t dn, int64_t cols_pad,
               StepParams sp, __half* __restrict__ D, float* __restrict__ cf,
-              ColExact* __restrict__ ci, unsigned long long* __restrict__ vd_max,
-              unsigned long long* __restrict__ vd_min_key)
+              ColExact* __restrict__ ci)
 {
     constexpr int G = K / 8;
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -277,7 +298,7 @@ gather_kernel(const uint8_t* __restrict__ img, int N, int B, int L, int per,
         }
     }
     const int n = B * B;
-    int s = 0, s2 = 0;
+    int s = 0, s2sum = 0;
     __align__(16) __half hv[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
@@ -285,16 +306,16 @@ gather_kernel(const uint8_t* __restrict__ img, int N, int B, int L, int per,
         int val = 0;
         if (real && k < n) {
             const int i = k / B, j = k % B;
-            const uint8_t* p0 = img + (int64_t)(y + 2 * i) * N + x + 2 * j;
-            const int d = (int)p0[0] + p0[1] + p0[N] + p0[N + 1];
+            const int d = box[(int64_t)(y + 2 * i) * N + x + 2 * j];
             s += d;
-            s2 += d * d;
+            s2sum += d * d;
             val = d - kDomainCentre;
         }
         hv[e] = __int2half_rn(val);
     }
     *reinterpret_cast<uint4*>(D + tile_off(c, kg * 8, cols_pad, K)) =
         *reinterpret_cast<const uint4*>(hv);
+    int s2 = s2sum;
 #pragma unroll
     for (int m = 1; m < G; m <<= 1) {
         s += __shfl_xor_sync(0xffffffffu, s, m);
@@ -311,9 +332,6 @@ gather_kernel(const uint8_t* __restrict__ img, int N, int B, int L, int per,
             grp[(1 + t) * 4] =
                 __double2float_rn((double)sp.p[t] * sp.p[t] * (double)vd / (double)n);
         ci[c] = ColExact{s, s2};
-        atomicMax(vd_max, (unsigned long long)vd);
-        // (Vd << 24 | c): the smallest Vd, first index on ties (Vd < 2^36, c < 2^24)
-        atomicMin(vd_min_key, ((unsigned long long)vd << 24) | (unsigned long long)c);
     } else {
         grp[0] = 0.0f;
         for (int t = 0; t < sp.ns; ++t) grp[(1 + t) * 4] = __int_as_float(0x7f800000);
@@ -321,7 +339,49 @@ gather_kernel(const uint8_t* __restrict__ img, int N, int B, int L, int per,
     }
 }
 
-cudaError_t launch_gather(const uint8_t* img, int N, int B, int L, int per,
+// Pool-wide reductions over the per-domain sums: max Vd and the key
+// (Vd << 24 | c) of the smallest Vd (first index on ties; Vd < 2^36,
+// c < 2^24).  Grid-stride; one atomic per block.
+__global__ void __launch_bounds__(256)
+pool_stats_kernel(const ColExact* __restrict__ ci, int64_t dn, int n,
+                  unsigned long long* __restrict__ vd_max,
+                  unsigned long long* __restrict__ vd_min_key)
+{
+    unsigned long long mx = 0, mn = ~0ull;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < dn;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const ColExact e = ci[c];
+        const unsigned long long vd =
+            (unsigned long long)((long long)n * e.sd2 - (long long)e.sd * e.sd);
+        mx = vd > mx ? vd : mx;
+        const unsigned long long key = (vd << 24) | (unsigned long long)c;
+        mn = key < mn ? key : mn;
+    }
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        const unsigned long long omx = __shfl_xor_sync(0xffffffffu, mx, m);
+        const unsigned long long omn = __shfl_xor_sync(0xffffffffu, mn, m);
+        mx = omx > mx ? omx : mx;
+        mn = omn < mn ? omn : mn;
+    }
+    __shared__ unsigned long long smx[8], smn[8];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        smx[w] = mx;
+        smn[w] = mn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+            mx = smx[i] > mx ? smx[i] : mx;
+            mn = smn[i] < mn ? smn[i] : mn;
+        }
+        atomicMax(vd_max, mx);
+        atomicMin(vd_min_key, mn);
+    }
+}
+
+cudaError_t launch_gather(const uint16_t* s2img, int N, int B, int L, int per,
                           const uint32_t* pool_xy, int64_t dn, int64_t cols_pad, int K,
                           const StepParams& sp, __half* D, float* cf, ColExact* ci,
                           unsigned long long* vd_max, unsigned long long* vd_min_key,
@@ -331,18 +391,24 @@ cudaError_t launch_gather(const uint8_t* img, int N, int B, int L, int per,
     const unsigned blocks = (unsigned)((threads + 255) / 256);
     switch (K) {
         case 16:
-            gather_kernel<16><<<blocks, 256, 0, s>>>(img, N, B, L, per, pool_xy, dn, cols_pad,
-                                                     sp, D, cf, ci, vd_max, vd_min_key);
+            gather_kernel<16><<<blocks, 256, 0, s>>>(s2img, N, B, L, per, pool_xy, dn, cols_pad,
+                                                     sp, D, cf, ci);
             break;
         case 64:
-            gather_kernel<64><<<blocks, 256, 0, s>>>(img, N, B, L, per, pool_xy, dn, cols_pad,
-                                                     sp, D, cf, ci, vd_max, vd_min_key);
+            gather_kernel<64><<<blocks, 256, 0, s>>>(s2img, N, B, L, per, pool_xy, dn, cols_pad,
+                                                     sp, D, cf, ci);
             break;
         case 256:
-            gather_kernel<256><<<blocks, 256, 0, s>>>(img, N, B, L, per, pool_xy, dn, cols_pad,
-                                                      sp, D, cf, ci, vd_max, vd_min_key);
+            gather_kernel<256><<<blocks, 256, 0, s>>>(s2img, N, B, L, per, pool_xy, dn, cols_pad,
+                                                      sp, D, cf, ci);
             break;
         default: return cudaErrorInvalidValue;
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // pool-wide max Vd (filter bound) and (min Vd, first index) key (flat ranges)
+    if (dn > 0) {
+        pool_stats_kernel<<<256, 256, 0, s>>>(ci, dn, B * B, vd_max, vd_min_key);
     }
     return cudaGetLastError();
 }
@@ -355,8 +421,8 @@ cudaError_t launch_gather(const uint8_t* img, int N, int B, int L, int per,
 __global__ void __launch_bounds__(256)
 range_prep_kernel(const uint8_t* __restrict__ img, int N, int B, const uint32_t* __restrict__ act,
                   int R, int Rpad, int64_t rows_pad, int K, StepParams sp,
-                  const unsigned long long* __restrict__ vd_max, __half* __restrict__ A,
-                  RowConst* __restrict__ rc)
+                  const unsigned long long* __restrict__ vd_max, int iso_major,
+                  __half* __restrict__ A, RowConst* __restrict__ rc)
 {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int rho = blockIdx.x * 8 + w;
@@ -395,7 +461,8 @@ range_prep_kernel(const uint8_t* __restrict__ img, int N, int B, const uint32_t*
             }
             hv[e] = __int2half_rn(val);
         }
-        *reinterpret_cast<uint4*>(A + tile_off((int64_t)rho * 8 + k, kg * 8, rows_pad, K)) =
+        const int64_t row = iso_major ? (int64_t)k * Rpad + rho : (int64_t)rho * 8 + k;
+        *reinterpret_cast<uint4*>(A + tile_off(row, kg * 8, rows_pad, K)) =
             *reinterpret_cast<const uint4*>(hv);
     }
     if (lane == 0) {
@@ -420,13 +487,13 @@ range_prep_kernel(const uint8_t* __restrict__ img, int N, int B, const uint32_t*
 
 cudaError_t launch_range_prep(const uint8_t* img, int N, int B, const uint32_t* act, int R,
                               int64_t rows_pad, int K, const StepParams& sp,
-                              const unsigned long long* vd_max, __half* A, RowConst* rc,
-                              cudaStream_t s)
+                              const unsigned long long* vd_max, int iso_major, __half* A,
+                              RowConst* rc, cudaStream_t s)
 {
     const int Rpad = (int)(rows_pad / 8);
     if (Rpad == 0) return cudaSuccess;
     range_prep_kernel<<<(Rpad + 7) / 8, 256, 0, s>>>(img, N, B, act, R, Rpad, rows_pad, K, sp,
-                                                     vd_max, A, rc);
+                                                     vd_max, iso_major, A, rc);
     return cudaGetLastError();
 }
 
