@@ -347,6 +347,94 @@ def run_gpu(args):
     return 0
 
 
+# ---------------------------------------------------------------- batching form
+BATCH_DESC = ("batch64: 64 uint8 1/f images, seeds 100..163, side uniform over {128, 256, 384, "
+              "512, 768, 1024}, alpha uniform in [1.5, 2.5]; quadtree 16->8->4, L=2, entropy > "
+              "4.0 bits, S {0.1},{0.2,0.4},{0.3,0.8}, RMS tol 8")
+
+
+def run_batch(args):
+    """The 64-image batching workload: every image in one fic_encode_batch
+    call (one grouped contraction launch per quadtree step), against the same
+    images encoded one call at a time."""
+    import torch
+    import paper_1502_00324_gb300 as pkg
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    imgs = fic_synth.batch_images(64)
+    dimgs = [torch.from_numpy(im).to(dev) for im in imgs]
+    ss = pkg.paper_ssets(16, 4)
+    args_enc = (16, 4, 2, 4.0, ss, 8.0)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def batch():
+        return pkg.fic_encode_batch(dimgs, *args_enc, stream=stream)
+
+    def one_by_one():
+        return [pkg.fic_encode_ex(d, d.shape[0], *args_enc, stream=stream) for d in dimgs]
+
+    def timed(fn, steps, warmup, timing=False):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        pkg.fic_stats_reset(timing=timing)
+        ms, out = [], None
+        for _ in range(steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms, out, pkg.fic_stats_read()
+
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    ms_b, out_b, st_b = timed(batch, args.steps, args.warmup, True)
+    clocks = sampler.stop()
+    ms_s, out_s, _ = timed(one_by_one, max(1, min(args.steps, 3)), 1)
+    identical = all(np.array_equal(a.codes, b.codes) for a, b in zip(out_b, out_s))
+    matches = sum(r.total_matches for r in out_b)
+    med_b = statistics.median(ms_b)
+    med_s = statistics.median(ms_s)
+    launches = sum(v["launches"] for v in st_b.values() if isinstance(v, dict))
+    tc = st_b["contract_tc"]
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak_tf = peaks.get("bf16_tflops", 1900.0)
+    achieved = tc["flops"] / (tc["ms"] / 1e3) / 1e12 if tc["ms"] > 0 else None
+    line = {
+        "metric": "aggregate Gmatch/s and ms per image, 64-image batch", "workload": "batch64",
+        "value": matches / (med_b / 1e3) / 1e9, "unit": "Gmatch/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": med_b,
+        "higher_is_better": True, "dtype": "fp16->fp32 (exact int)", "data": "synthetic",
+        "config": {"workload": BATCH_DESC, "images": len(imgs),
+                   "sides": sorted(int(i.shape[0]) for i in imgs),
+                   "l2": "flushed between timed steps (512 MiB write)",
+                   "timed": "device-resident images -> host records (D2H of records inside)"},
+        "ms_per_image": med_b / len(imgs), "images_per_s": len(imgs) / (med_b / 1e3),
+        "matches_per_batch": matches,
+        "one_call_per_image": {"ms_per_batch": med_s,
+                               "value": matches / (med_s / 1e3) / 1e9, "unit": "Gmatch/s"},
+        "batch_over_one_by_one": med_s / med_b,
+        "codes_identical_batch_vs_single": identical,
+        "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in st_b.items()
+                               if isinstance(v, dict)},
+        "contraction_tflops": achieved, "contraction_frac_of_bf16_peak":
+            (achieved / peak_tf) if achieved else None,
+        "gpu_launches": int(launches / args.steps), "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -355,11 +443,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--legs", default="tensor,plain,e2e,cpu",
                     help="measurements to run (profiling runs use 'tensor' alone)")
+    ap.add_argument("--workload", default="precision512", choices=["precision512", "batch64"],
+                    help="precision512: the headline line; batch64: the 64-image batching form")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     import __graft_entry__
     __graft_entry__.build()
+    if args.workload == "batch64":
+        return run_batch(args)
     return run_gpu(args)
 
 

@@ -151,6 +151,21 @@ int fic_encode(const uint8_t* img, int N, int B_max, int B_min, int L,
 int fic_encode_ex(const uint8_t* img, const fic_params* p, fic_code* codes_out,
                   int64_t codes_cap, fic_result* out, void* stream);
 
+/* fic_encode_batch -- encode n_img images of (possibly different) sides
+ * Ns[i] with one parameter set (p->N is ignored; every Ns[i] must satisfy
+ * the rules of p->N).  The images share each quadtree step: pools, gathers
+ * and split decisions run per image, the range-domain contraction of a step
+ * runs as ONE launch over the work of every image.  Each image's records
+ * are identical to those of fic_encode_ex on that image alone.
+ *   imgs   host array of n_img pointers, each host or device, N_i*N_i bytes.
+ *   Ns     host array of n_img sides.
+ *   outs   host array of n_img results; each outs[i].codes is a host array
+ *          allocated by the library (free each with fic_result_free).
+ * On error every outs[i] is left without codes.  The paper encodes one
+ * image at a time (Sec. 3); batching is this library's serving form. */
+int fic_encode_batch(int n_img, const uint8_t* const* imgs, const int* Ns,
+                     const fic_params* p, fic_result* outs, void* stream);
+
 /* fic_decode -- rebuild the image from a result on the GPU (Sec. 2): start
  * from a constant 128 image; each pass rebuilds every range from its domain
  * in the previous pass, pixel = clamp(round_half_up((2 o_q + 1) +
@@ -196,6 +211,79 @@ int fic_domain_pool(const uint8_t* img, int N, int B, int L, double entropy_thre
 int fic_domain_pool_noalloc(const uint8_t* d_img, int N, int B, int L,
                             double entropy_thresh, uint32_t* d_pool_xy, int64_t cap,
                             int64_t* dn, double* d_entropy, int64_t* near, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* Request server (continuous batching)                                */
+/* ------------------------------------------------------------------ */
+/* A server owns a worker thread, a CUDA stream and device workspaces on
+ * the device current at creation.  Requests (images of any valid side,
+ * one parameter set per server) wait in a FIFO queue; between quadtree
+ * steps the worker admits queued images while a workspace slot is free
+ * and the device bytes of the admitted images (an estimate per image from
+ * N, B_max..B_min, L and the engine) stay within the HBM budget.  Each
+ * worker iteration advances EVERY admitted image by one quadtree step,
+ * whatever step it is at, with one grouped contraction launch per step
+ * present (fic_encode_batch's engine), so images that arrive while others
+ * are on the GPU join the next launch.  Pools, active ranges and partial
+ * records stay on the device until an image's last step; then its records
+ * are ordered and copied to a host array.  Each image's records are
+ * identical to those of fic_encode_ex on that image alone.  The paper
+ * encodes one image at a time (Sec. 3); the server is this library's
+ * serving form. */
+typedef struct fic_server fic_server;
+
+typedef struct {
+    int64_t hbm_budget;    /* device bytes for admitted images; 0 = half of
+                              the free device memory at creation          */
+    int32_t max_inflight;  /* admitted images at once (slots); 0 = 64      */
+    int32_t max_queue;     /* waiting requests; 0 = 65536.  A submit
+                              beyond it returns FIC_EBUSY                 */
+} fic_server_config;
+
+typedef struct {
+    double submit_ms;      /* host steady clock, ms since server creation */
+    double admit_ms;       /* taken from the queue onto the device         */
+    double done_ms;        /* records on the host                          */
+    int32_t steps;         /* worker iterations the image took part in     */
+    int32_t shared_steps;  /* ... of which with other images in flight     */
+} fic_timing;
+
+typedef struct {
+    int64_t submitted, completed, failed;
+    int64_t queued, inflight;          /* now                              */
+    int64_t iterations;                /* worker iterations (steps)        */
+    int64_t contraction_launches;
+    double mean_inflight;              /* images per iteration, mean       */
+    int64_t peak_inflight;
+    int64_t hbm_in_use, hbm_peak;      /* estimated bytes held by slots    */
+    int64_t hbm_budget;
+    int64_t matches;                   /* (range, domain, isometry) total  */
+    double busy_ms;                    /* worker time with images in flight*/
+} fic_server_stats;
+
+/* fic_server_create -- p: host, copied (p->N is ignored); cfg: host, may be
+ * NULL.  *out receives the server.  Returns FIC_EINVAL for a bad parameter
+ * set, FIC_ENODEV without an sm_103 device current. */
+int fic_server_create(const fic_params* p, const fic_server_config* cfg, fic_server** out);
+/* fic_server_submit -- queue one N x N image.  img: host pointer (copied
+ * before return) or device pointer (NOT copied: its contents must be
+ * complete on the device before the call, e.g. its producing stream
+ * synchronised, and stay valid and unchanged until the ticket completes;
+ * the server reads it from its own stream).  *ticket receives an id > 0.
+ * FIC_EINVAL: N invalid for the parameter set; FIC_EBUSY: queue full. */
+int fic_server_submit(fic_server* s, const uint8_t* img, int N, int64_t* ticket);
+/* fic_server_poll -- wait up to wait_ms (0: do not wait, < 0: forever) for
+ * a ticket.  FIC_OK: *out receives the result (host codes owned by the
+ * caller: fic_result_free) and *timing (may be NULL) its times; the ticket
+ * is then forgotten.  FIC_ENOTREADY: still queued or running.  A failed
+ * encode returns its status once.  FIC_EINVAL: unknown ticket. */
+int fic_server_poll(fic_server* s, int64_t ticket, int wait_ms, fic_result* out,
+                    fic_timing* timing);
+/* fic_server_stats_read -- counters since creation. */
+int fic_server_stats_read(fic_server* s, fic_server_stats* out);
+/* fic_server_destroy -- finish the images in flight, fail the queued ones,
+ * stop the worker and free every resource (unpolled results included). */
+int fic_server_destroy(fic_server* s);
 
 /* Frees the library-owned parts of a result (the code array when
  * owns_codes).  Safe on a zeroed struct. */

@@ -10,9 +10,11 @@ from .fic import (  # noqa: F401
     CODE_DTYPE,
     Encoded,
     FicError,
+    Server,
     fic_decode,
     fic_domain_pool,
     fic_encode,
+    fic_encode_batch,
     fic_encode_ex,
     fic_stats_read,
     fic_stats_reset,

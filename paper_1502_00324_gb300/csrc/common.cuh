@@ -108,6 +108,39 @@ __device__ __forceinline__ long long exact_h(int cprime, int sr, int sd, int sd2
 }
 
 // ---------------------------------------------------------------------------
+// One image's quadtree step inside a grouped contraction launch.  Work items
+// of problem p are item_start .. item_start + n_mtiles * n_chunks - 1, chunk
+// major (item = item_start + chunk * n_mtiles + mtile).
+// ---------------------------------------------------------------------------
+struct Problem {
+    const __half* A;      // range operand (layout of the engine)
+    const __half* D;      // pool operand
+    const float* cf;      // column filter constants
+    const ColExact* ci;   // exact column sums
+    const RowConst* rc;   // per active range
+    Best* part;           // partial bests: range * parts_per_range + slot
+    long long* gbest;     // shared best key per row (or per range)
+    int64_t rows_pad;     // rows of A
+    int64_t cols_pad;     // pool columns, padded
+    int R, dn;            // active ranges, pool size
+    int n_mtiles, n_ct;   // M tiles, N tiles
+    int n_chunks, per_chunk;
+    int item_start;
+    int pad;
+};
+
+__device__ __forceinline__ int find_problem(const Problem* __restrict__ probs, int n, int item)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (probs[mid].item_start <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
 // FP32 filter.  For column c and S_s = p_s/q the filter value is
 //   f = fma(-8 p q, t', beta_s),  t' = fma(-a, m_c, C'),
 // with a = sum A' (exact), m_c = sum D'/n (exact), beta_s = fl(p^2 Vd / n).

@@ -15,20 +15,29 @@ namespace fic {
 
 template <int K, int NS>
 __global__ void __launch_bounds__(256)
-contract_plain_kernel(const __half* __restrict__ A, int64_t rows_pad,
-                      const __half* __restrict__ D, int64_t cols_pad,
-                      const float* __restrict__ cf, const ColExact* __restrict__ ci,
-                      const RowConst* __restrict__ rc, int R, int dn, int ctiles_per_chunk,
-                      int n_ctiles, int n_chunks, Best* __restrict__ part,
-                      long long* __restrict__ gbest, const __grid_constant__ StepParams sp)
+contract_plain_kernel(const Problem* __restrict__ probs, int n_probs,
+                      const __grid_constant__ StepParams sp)
 {
+    // one block per work item; M tiles vary fastest, so the blocks running
+    // together share one column chunk and a range's earlier chunks finish
+    // before its later ones start
+    const Problem& Q = probs[find_problem(probs, n_probs, (int)blockIdx.x)];
+    const __half* __restrict__ A = Q.A;
+    const __half* __restrict__ D = Q.D;
+    const float* __restrict__ cf = Q.cf;
+    const ColExact* __restrict__ ci = Q.ci;
+    const RowConst* __restrict__ rc = Q.rc;
+    Best* __restrict__ part = Q.part;
+    long long* __restrict__ gbest = Q.gbest;
+    const int64_t rows_pad = Q.rows_pad, cols_pad = Q.cols_pad;
+    const int R = Q.R, dn = Q.dn, ctiles_per_chunk = Q.per_chunk, n_ctiles = Q.n_ct,
+              n_chunks = Q.n_chunks;
+    const int local = (int)blockIdx.x - Q.item_start;
+    const int mtile = local % Q.n_mtiles, chunk = local / Q.n_mtiles;
     __shared__ __align__(16) int sA[16][128];
     __shared__ __align__(16) int sD[16][128];
     const int tid = threadIdx.x;
     const int ty = tid >> 4, tx = tid & 15;
-    // M tiles vary fastest, so the blocks running together share one column
-    // chunk and a range's earlier chunks finish before its later ones start
-    const int mtile = blockIdx.x, chunk = blockIdx.y;
     const int range = mtile * kRangesPerTile + ty;
     const RowConst r = range < R ? rc[range] : RowConst{0, 0, 0.f, 0.f};
     // flat ranges are resolved in the split step (h = p^2 Vd)
@@ -120,20 +129,13 @@ contract_plain_kernel(const __half* __restrict__ A, int64_t rows_pad,
 template <int K>
 static cudaError_t launch_plain_k(const ContractArgs& a, cudaStream_t s)
 {
-    dim3 grid((unsigned)(a.rows_pad / kMTile), a.n_chunks);
-    const int n_ctiles = (int)(a.cols_pad / 128);
-    const int per = a.ctiles_per_chunk;
-#define FIC_PLAIN_CASE(NSV)                                                              \
-    contract_plain_kernel<K, NSV><<<grid, 256, 0, s>>>(                                  \
-        a.A, a.rows_pad, a.D, a.cols_pad, a.cf, a.ci, a.rc, a.R, a.dn, per, n_ctiles,   \
-        a.n_chunks, a.part, a.gbest, a.sp)
+    if (a.n_items == 0) return cudaSuccess;
     switch (a.sp.ns) {
-        case 1: FIC_PLAIN_CASE(1); break;
-        case 2: FIC_PLAIN_CASE(2); break;
-        case 3: FIC_PLAIN_CASE(3); break;
-        default: FIC_PLAIN_CASE(0); break;
+        case 1: contract_plain_kernel<K, 1><<<a.n_items, 256, 0, s>>>(a.probs, a.n_probs, a.sp); break;
+        case 2: contract_plain_kernel<K, 2><<<a.n_items, 256, 0, s>>>(a.probs, a.n_probs, a.sp); break;
+        case 3: contract_plain_kernel<K, 3><<<a.n_items, 256, 0, s>>>(a.probs, a.n_probs, a.sp); break;
+        default: contract_plain_kernel<K, 0><<<a.n_items, 256, 0, s>>>(a.probs, a.n_probs, a.sp); break;
     }
-#undef FIC_PLAIN_CASE
     return cudaGetLastError();
 }
 

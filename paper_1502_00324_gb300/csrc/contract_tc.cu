@@ -59,18 +59,13 @@ constexpr int kMaxRegsRaw = 16384 / (32 * kWarpsPerSubPartition) / 8 * 8;
 constexpr int kMaxRegs = kMaxRegsRaw > 255 ? 255 : kMaxRegsRaw;
 constexpr uint32_t kTmemCols = 512;
 
+// Launch parameters; per-image data comes from the problem table (A rows
+// are (range, isometry) pairs, row 8 range + k; gbest per row).
 struct TcParams {
-    const __half* A;
-    int64_t rows_pad;
-    const __half* D;
-    int64_t cols_pad;
-    const float* cf;
-    const ColExact* ci;
-    const RowConst* rc;
-    Best* part;
-    long long* gbest;
+    const Problem* probs;
+    int n_probs, n_items;
     int* err;
-    int R, dn, n_chunks, per_chunk, n_ct, n_mtiles, n_items, nstage, ncf;
+    int nstage, ncf;
 };
 
 template <int K, int NS>
@@ -143,15 +138,17 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
         int64_t it = 0, tcount = 0, cfi = 0, icount = 0;
         bool ok = true;
         for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
-            const int chunk = item / P.n_mtiles, mtile = item % P.n_mtiles;
-            const int ct0 = chunk * P.per_chunk;
-            const int ct1 = min(P.n_ct, ct0 + P.per_chunk);
+            const Problem& Q = P.probs[find_problem(P.probs, P.n_probs, item)];
+            const int local = item - Q.item_start;
+            const int chunk = local / Q.n_mtiles, mtile = local % Q.n_mtiles;
+            const int ct0 = chunk * Q.per_chunk;
+            const int ct1 = min(Q.n_ct, ct0 + Q.per_chunk);
             if (!(ok = mbar_wait_warp(a_empty, (uint32_t)((icount & 1) ^ 1), err, kWaitCycles))) break;
             if (elect_one()) {
                 mbar_expect_tx(a_full, NKB * kAKBBytes);
                 for (int kb = 0; kb < NKB; ++kb)
                     bulk_g2s(smem_u32(sA + kb * kAKBBytes),
-                             P.A + ((int64_t)kb * P.rows_pad * KB + (int64_t)mtile * 128 * KB),
+                             Q.A + ((int64_t)kb * Q.rows_pad * KB + (int64_t)mtile * 128 * KB),
                              kAKBBytes, a_full);
             }
             __syncwarp();
@@ -162,7 +159,7 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
                 if (!(ok = mbar_wait_warp(cfe(cb), cph ^ 1, err, kWaitCycles))) break;
                 if (elect_one()) {
                     mbar_expect_tx(cff(cb), cf_bytes);
-                    bulk_g2s(smem_u32(sCF + (size_t)cb * cf_bytes), P.cf + (int64_t)ct * kN * sp.cw,
+                    bulk_g2s(smem_u32(sCF + (size_t)cb * cf_bytes), Q.cf + (int64_t)ct * kN * sp.cw,
                              cf_bytes, cff(cb));
                 }
                 __syncwarp();
@@ -174,7 +171,7 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
                     if (elect_one()) {
                         mbar_expect_tx(full(s), kBStageBytes);
                         bulk_g2s(smem_u32(sB + (size_t)s * kBStageBytes),
-                                 P.D + ((int64_t)kb * P.cols_pad * KB + (int64_t)ct * kN * KB),
+                                 Q.D + ((int64_t)kb * Q.cols_pad * KB + (int64_t)ct * kN * KB),
                                  kBStageBytes, full(s));
                     }
                     __syncwarp();
@@ -198,9 +195,10 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
         int64_t it = 0, tcount = 0, icount = 0;
         bool ok = true;
         for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
-            const int chunk = item / P.n_mtiles;
-            const int ct0 = chunk * P.per_chunk;
-            const int ct1 = min(P.n_ct, ct0 + P.per_chunk);
+            const Problem& Q = P.probs[find_problem(P.probs, P.n_probs, item)];
+            const int chunk = (item - Q.item_start) / Q.n_mtiles;
+            const int ct0 = chunk * Q.per_chunk;
+            const int ct1 = min(Q.n_ct, ct0 + Q.per_chunk);
             if (!(ok = mbar_wait_warp(a_full, (uint32_t)(icount & 1), err, kWaitCycles))) break;
             tc_fence_after();
             for (int ct = ct0; ct < ct1 && ok; ++ct) {
@@ -249,18 +247,22 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
         int64_t tcount = 0;
         bool ok = true;
         for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
-            const int chunk = item / P.n_mtiles, mtile = item % P.n_mtiles;
-            const int ct0 = chunk * P.per_chunk;
-            const int ct1 = min(P.n_ct, ct0 + P.per_chunk);
+            const Problem& Q = P.probs[find_problem(P.probs, P.n_probs, item)];
+            const int local = item - Q.item_start;
+            const int chunk = local / Q.n_mtiles, mtile = local % Q.n_mtiles;
+            const int ct0 = chunk * Q.per_chunk;
+            const int ct1 = min(Q.n_ct, ct0 + Q.per_chunk);
+            const ColExact* qci = Q.ci;
+            const int qdn = Q.dn;
             const int row = mtile * 128 + quad * 32 + lane;
             const int range = row >> 3;
             const unsigned iso = (unsigned)(row & 7);
-            const RowConst r = range < P.R ? P.rc[range] : RowConst{0, 0, 0.f, 0.f};
+            const RowConst r = range < Q.R ? Q.rc[range] : RowConst{0, 0, 0.f, 0.f};
             // flat ranges are resolved in the split step (h = p^2 Vd)
-            const bool valid = range < P.R && !range_is_flat(r, sp.n);
+            const bool valid = range < Q.R && !range_is_flat(r, sp.n);
             RowState st;
             row_state_init(st);
-            if (valid) row_state_seed(st, P.gbest + row, inv_n, r.delta);
+            if (valid) row_state_seed(st, Q.gbest + row, inv_n, r.delta);
             for (int ct = ct0; ct < ct1; ++ct) {
                 const int acc = (int)(tcount & 1);
                 const uint32_t ph = (uint32_t)((tcount >> 1) & 1);
@@ -303,7 +305,7 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
                     }
                     if (mn <= st.thr)
                         epi_pass2<NS, 8>(st, cur, mn, cfs, g0, 1, ct * kN, iso, -r.a, r.delta,
-                                         inv_n, r.sr, P.ci, P.dn, &sp);
+                                         inv_n, r.sr, qci, qdn, &sp);
                 }
 #else
 #pragma unroll 1
@@ -320,7 +322,7 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
                     }
                     if (valid)
                         epi_groups<NS, 8>(st, x, cfs, (cq * kColsPerEpiWarp + 32 * b) / 4, 1,
-                                          ct * kN, iso, -r.a, r.delta, inv_n, r.sr, P.ci, P.dn,
+                                          ct * kN, iso, -r.a, r.delta, inv_n, r.sr, qci, qdn,
                                           &sp);
                 }
 #endif
@@ -329,7 +331,7 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
                 ++tcount;
             }
             if (!ok) break;
-            if (valid) row_state_publish(st, P.gbest + row);
+            if (valid) row_state_publish(st, Q.gbest + row);
             // best over the 8 isometries of each range (lanes 8j .. 8j+7)
             long long h = st.h;
             unsigned idx = st.idx;
@@ -341,7 +343,7 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
                 b.h = h;
                 b.idx = idx;
                 b.pad = 0;
-                P.part[(int64_t)range * (kPartsPerChunk * P.n_chunks) + kPartsPerChunk * chunk + cq] = b;
+                Q.part[(int64_t)range * (kPartsPerChunk * Q.n_chunks) + kPartsPerChunk * chunk + cq] = b;
             }
         }
     }
@@ -389,23 +391,10 @@ cudaError_t launch_tc_kns(const ContractArgs& a, cudaStream_t s)
                                          (int)smem);
     if (e != cudaSuccess) return e;
     TcParams P;
-    P.A = a.A;
-    P.rows_pad = a.rows_pad;
-    P.D = a.D;
-    P.cols_pad = a.cols_pad;
-    P.cf = a.cf;
-    P.ci = a.ci;
-    P.rc = a.rc;
-    P.part = a.part;
-    P.gbest = a.gbest;
+    P.probs = a.probs;
+    P.n_probs = a.n_probs;
+    P.n_items = a.n_items;
     P.err = a.err;
-    P.R = a.R;
-    P.dn = a.dn;
-    P.n_chunks = a.n_chunks;
-    P.per_chunk = a.ctiles_per_chunk;
-    P.n_ct = (int)(a.cols_pad / kN);
-    P.n_mtiles = (int)(a.rows_pad / 128);
-    P.n_items = P.n_mtiles * a.n_chunks;
     P.nstage = nstage;
     P.ncf = ncf;
     const int grid = P.n_items < a.grid_ctas ? P.n_items : a.grid_ctas;

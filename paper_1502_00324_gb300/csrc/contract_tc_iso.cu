@@ -48,18 +48,13 @@ constexpr int kMaxSlots = 4;
 constexpr int kWarpsPerSubPartition = (kThreads / 32 + 3) / 4;
 constexpr int kMaxRegs = 16384 / (32 * kWarpsPerSubPartition) / 8 * 8;
 
+// Launch parameters; per-image data comes from the problem table (A is
+// iso-major: row k * (rows_pad / 8) + range; gbest and partials per range).
 struct IsoParams {
-    const __half* A;       // iso-major rows (k * Rpad + range), tile layout
-    int64_t Rpad;          // ranges padded to 128
-    const __half* D;
-    int64_t cols_pad;
-    const float* cf;
-    const ColExact* ci;
-    const RowConst* rc;
-    Best* part;
-    long long* gbest;      // per range
+    const Problem* probs;
+    int n_probs, n_items;
     int* err;
-    int R, dn, n_chunks, per_chunk, n_ct, n_mtiles, n_items, nstage, ncf;
+    int nstage, ncf;
 };
 
 __device__ __forceinline__ float fmax3(float a, float b, float c)
@@ -253,15 +248,18 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
         int64_t it = 0, cfi = 0, icount = 0;
         bool ok = true;
         for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
-            const int chunk = item / P.n_mtiles, mtile = item % P.n_mtiles;
-            const int ct0 = chunk * P.per_chunk;
-            const int ct1 = min(P.n_ct, ct0 + P.per_chunk);
+            const Problem& Q = P.probs[find_problem(P.probs, P.n_probs, item)];
+            const int local = item - Q.item_start;
+            const int chunk = local / Q.n_mtiles, mtile = local % Q.n_mtiles;
+            const int ct0 = chunk * Q.per_chunk;
+            const int ct1 = min(Q.n_ct, ct0 + Q.per_chunk);
+            const int64_t rpad = Q.rows_pad / 8;
             if (!(ok = mbar_wait_warp(a_empty, (uint32_t)((icount & 1) ^ 1), err, kWaitCycles))) break;
             if (elect_one()) {
                 mbar_expect_tx(a_full, 8 * kAIsoBytes);
                 for (int k = 0; k < 8; ++k)
                     bulk_g2s(smem_u32(sA + k * kAIsoBytes),
-                             P.A + ((int64_t)k * P.Rpad + (int64_t)mtile * 128) * K, kAIsoBytes,
+                             Q.A + ((int64_t)k * rpad + (int64_t)mtile * 128) * K, kAIsoBytes,
                              a_full);
             }
             __syncwarp();
@@ -272,7 +270,7 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
                 if (!(ok = mbar_wait_warp(cfe(cb), cph ^ 1, err, kWaitCycles))) break;
                 if (elect_one()) {
                     mbar_expect_tx(cff(cb), cf_bytes);
-                    bulk_g2s(smem_u32(sCF + (size_t)cb * cf_bytes), P.cf + (int64_t)ct * kN * sp.cw,
+                    bulk_g2s(smem_u32(sCF + (size_t)cb * cf_bytes), Q.cf + (int64_t)ct * kN * sp.cw,
                              cf_bytes, cff(cb));
                 }
                 __syncwarp();
@@ -282,7 +280,7 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
                 if (!(ok = mbar_wait_warp(empty(s), sph ^ 1, err, kWaitCycles))) break;
                 if (elect_one()) {
                     mbar_expect_tx(full(s), kBStageBytes);
-                    bulk_g2s(smem_u32(sB + (size_t)s * kBStageBytes), P.D + (int64_t)ct * kN * K,
+                    bulk_g2s(smem_u32(sB + (size_t)s * kBStageBytes), Q.D + (int64_t)ct * kN * K,
                              kBStageBytes, full(s));
                 }
                 __syncwarp();
@@ -306,9 +304,10 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
         int64_t it = 0, pcount = 0, icount = 0;
         bool ok = true;
         for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
-            const int chunk = item / P.n_mtiles;
-            const int ct0 = chunk * P.per_chunk;
-            const int ct1 = min(P.n_ct, ct0 + P.per_chunk);
+            const Problem& Q = P.probs[find_problem(P.probs, P.n_probs, item)];
+            const int chunk = (item - Q.item_start) / Q.n_mtiles;
+            const int ct0 = chunk * Q.per_chunk;
+            const int ct1 = min(Q.n_ct, ct0 + Q.per_chunk);
             if (!(ok = mbar_wait_warp(a_full, (uint32_t)(icount & 1), err, kWaitCycles))) break;
             tc_fence_after();
             for (int ct = ct0; ct < ct1 && ok; ++ct) {
@@ -361,16 +360,20 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
         int64_t it = 0, pcount = 0;
         bool ok = true;
         for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
-            const int chunk = item / P.n_mtiles, mtile = item % P.n_mtiles;
-            const int ct0 = chunk * P.per_chunk;
-            const int ct1 = min(P.n_ct, ct0 + P.per_chunk);
+            const Problem& Q = P.probs[find_problem(P.probs, P.n_probs, item)];
+            const int local = item - Q.item_start;
+            const int chunk = local / Q.n_mtiles, mtile = local % Q.n_mtiles;
+            const int ct0 = chunk * Q.per_chunk;
+            const int ct1 = min(Q.n_ct, ct0 + Q.per_chunk);
+            const ColExact* qci = Q.ci;
+            const int qdn = Q.dn;
             const int range = mtile * 128 + quad * 32 + lane;
-            const RowConst r = range < P.R ? P.rc[range] : RowConst{0, 0, 0.f, 0.f};
+            const RowConst r = range < Q.R ? Q.rc[range] : RowConst{0, 0, 0.f, 0.f};
             // flat ranges are resolved in the split step (h = p^2 Vd)
-            const bool valid = range < P.R && !range_is_flat(r, sp.n);
+            const bool valid = range < Q.R && !range_is_flat(r, sp.n);
             RowState st;
             row_state_init(st);
-            if (valid) row_state_seed(st, P.gbest + range, inv_n, r.delta);
+            if (valid) row_state_seed(st, Q.gbest + range, inv_n, r.delta);
             for (int ct = ct0; ct < ct1; ++ct) {
                 const int cb = (int)(it % ncf);
                 const uint32_t cph = (uint32_t)((it / ncf) & 1);
@@ -399,7 +402,7 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
                             const float mn = iso_pass1<NS, kPass>(x, cfs, g0, -r.a, sp);
                             if (mn <= st.thr)
                                 iso_pass2<NS, kPass>(st, x, mn, cfs, g0, ct * kN, pass * kPass,
-                                                     -r.a, r.delta, inv_n, r.sr, P.ci, P.dn, &sp);
+                                                     -r.a, r.delta, inv_n, r.sr, qci, qdn, &sp);
                         }
                     }
                     ++pcount;
@@ -411,12 +414,12 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
             }
             if (!ok) break;
             if (valid) {
-                row_state_publish(st, P.gbest + range);
+                row_state_publish(st, Q.gbest + range);
                 Best b;
                 b.h = st.h;
                 b.idx = st.idx;
                 b.pad = 0;
-                P.part[(int64_t)range * (kPartsPerChunk * P.n_chunks) + kPartsPerChunk * chunk +
+                Q.part[(int64_t)range * (kPartsPerChunk * Q.n_chunks) + kPartsPerChunk * chunk +
                        hsel] = b;
             }
         }
@@ -465,23 +468,10 @@ cudaError_t launch_iso_kns(const ContractArgs& a, cudaStream_t s)
                                          (int)smem);
     if (e != cudaSuccess) return e;
     IsoParams P;
-    P.A = a.A;
-    P.Rpad = a.rows_pad / 8;
-    P.D = a.D;
-    P.cols_pad = a.cols_pad;
-    P.cf = a.cf;
-    P.ci = a.ci;
-    P.rc = a.rc;
-    P.part = a.part;
-    P.gbest = a.gbest;
+    P.probs = a.probs;
+    P.n_probs = a.n_probs;
+    P.n_items = a.n_items;
     P.err = a.err;
-    P.R = a.R;
-    P.dn = a.dn;
-    P.n_chunks = a.n_chunks;
-    P.per_chunk = a.ctiles_per_chunk;
-    P.n_ct = (int)(a.cols_pad / IsoShape<K>::N);
-    P.n_mtiles = (int)(P.Rpad / 128);
-    P.n_items = P.n_mtiles * a.n_chunks;
     P.nstage = nstage;
     P.ncf = ncf;
     const int grid = P.n_items < a.grid_ctas ? P.n_items : a.grid_ctas;

@@ -1,0 +1,677 @@
+// engine.cu -- the quadtree step driver (Sec. 2 quadtree, Sec. 3 pool, Sec.
+// 3.2 S) over any number of images, each at its own step:
+//   begin:  active ranges <- every B_max x B_max block in raster order
+//   step:   per job [entropy -> scan -> pool list] (threshold >= 0 only)
+//           -> per job domain gather (operand D', column constants)
+//           -> per job range prep (operand A' with inverse isometries)
+//           -> per quadtree step present: ONE contraction + scoring launch
+//              over the work items of all jobs at that step
+//           -> per job split decision -> scan -> records / children
+//   finish: record ordering (raster of top ranges, then TL, TR, BL, BR).
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "engine.h"
+#include "kernels.h"
+
+namespace fic {
+
+// ---------------------------------------------------------------------------
+// Instrumentation
+// ---------------------------------------------------------------------------
+StatsState g_stats;
+
+Launcher::Launcher(cudaStream_t s, bool allow_timing) : s_(s)
+{
+    std::lock_guard<std::mutex> g(g_stats.mu);
+    timing_ = allow_timing && g_stats.timing;
+}
+
+void Launcher::begin(int kind)
+{
+    kind_ = kind;
+    if (!timing_) return;
+    cur_.kind = kind;
+    cudaEventCreate(&cur_.a);
+    cudaEventCreate(&cur_.b);
+    cudaEventRecord(cur_.a, s_);
+}
+
+void Launcher::end(int launches, double flops, double bytes, int64_t matches)
+{
+    {
+        std::lock_guard<std::mutex> g(g_stats.mu);
+        g_stats.st.launches[kind_] += launches;
+        g_stats.st.flops[kind_] += flops;
+        g_stats.st.bytes[kind_] += bytes;
+        g_stats.st.matches += matches;
+    }
+    if (!timing_) return;
+    cudaEventRecord(cur_.b, s_);
+    pending_.push_back(cur_);
+}
+
+void Launcher::harvest()
+{
+    for (auto& p : pending_) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(p.b) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            std::lock_guard<std::mutex> g(g_stats.mu);
+            g_stats.st.ms[p.kind] += ms;
+        }
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    pending_.clear();
+}
+
+thread_local char g_last_error[160] = "";
+
+int to_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return FIC_OK;
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s", cudaGetErrorName(e),
+             cudaGetErrorString(e));
+    if (e == cudaErrorMemoryAllocation) return FIC_ENOMEM;
+    return FIC_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Buffers
+// ---------------------------------------------------------------------------
+cudaError_t DevBuf::ensure(size_t bytes)
+{
+    if (bytes <= cap) return cudaSuccess;
+    release();
+    size_t want = bytes + bytes / 8 + 256;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        return e;
+    }
+    cap = want;
+    return cudaSuccess;
+}
+
+void DevBuf::release()
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+}
+
+void ImageWork::release()
+{
+    DevBuf* all[] = {&img, &box2, &flags, &pos, &scan_tmp, &pool, &D, &cf, &ci, &A, &rc, &part,
+                     &gbest, &best, &split, &split_pos, &act0, &act1, &codes_tmp, &codes_out,
+                     &cellmap, &cellflag, &cellrank, &H};
+    for (DevBuf* b : all) b->release();
+}
+
+bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+namespace {
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+int ilog2i(int v)
+{
+    int r = 0;
+    while ((1 << r) < v) ++r;
+    return r;
+}
+
+bool valid_side(int b) { return b == 2 || b == 4 || b == 8 || b == 16; }
+
+StepParams make_step(const fic_sset& s, int n)
+{
+    StepParams sp;
+    memset(&sp, 0, sizeof(sp));
+    sp.n = n;
+    sp.q = s.q;
+    sp.ns = s.n_s;
+    sp.cw = 1 + s.n_s;  // m_c and one beta per S, in groups of 4 columns
+    for (int i = 0; i < s.n_s; ++i) {
+        sp.p[i] = s.p[i];
+        sp.kf[i] = (float)(8LL * s.p[i] * s.q);
+    }
+    return sp;
+}
+
+// Engine-dependent shape of one quadtree step.
+struct StepShape {
+    int B, n2, K;
+    StepParams sp;
+    bool iso;            // isometry-in-accumulator tensor kernel
+    int64_t tile_w;      // pool columns per tile
+    int parts_per_chunk; // partial bests per (range, column chunk)
+};
+
+StepShape step_shape(const fic_params& p, int lvl)
+{
+    StepShape h;
+    h.B = p.B_max >> lvl;
+    h.n2 = h.B * h.B;
+    h.K = k_pad(h.n2);
+    h.sp = make_step(p.S_sets[lvl], h.n2);
+    // 2x2 .. 8x8 ranges with up to 3 S values: ranges in TMEM lanes, one
+    // accumulator per isometry (iso-major A); otherwise rows are (range,
+    // isometry) pairs
+    const bool tc = p.engine == FIC_ENGINE_TENSOR;
+    h.iso = tc && contract_tc_iso_supports(h.K, h.sp.ns);
+    h.tile_w = h.iso ? contract_tc_iso_ntile(h.K) : (tc ? contract_tc_ntile() : kPlainNTile);
+    h.parts_per_chunk =
+        h.iso ? contract_tc_iso_parts_per_chunk() : (tc ? contract_tc_parts_per_chunk() : 1);
+    return h;
+}
+
+int64_t rows_pad_for(const StepShape& h, int64_t R)
+{
+    return h.iso ? 8 * round_up(R, 128) : round_up(8 * R, kMTile);
+}
+
+int64_t mtiles_for(const StepShape& h, int64_t rows_pad)
+{
+    return h.iso ? rows_pad / 8 / 128 : rows_pad / kMTile;
+}
+
+// Column chunking of the contraction: work items are (M tile, chunk of
+// column tiles).  Chunk counts stay <= 16 x SMs / M tiles, which bounds the
+// partial-best buffers.
+int64_t max_chunks(int sm_count, int64_t n_mtiles, int64_t n_ct)
+{
+    int64_t cap = (16LL * sm_count + n_mtiles - 1) / n_mtiles;
+    if (cap > 4096) cap = 4096;
+    if (cap > n_ct) cap = n_ct;
+    return cap < 1 ? 1 : cap;
+}
+
+// A problem alone in its launch: the chunk count that minimises the
+// estimated makespan over one item per SM (waves x tiles per item, plus a
+// per-item cost of refilling the pipeline).
+void choose_chunks_alone(int sm_count, int64_t n_mtiles, int64_t n_ct, int* n_chunks,
+                         int* per_chunk)
+{
+    const int64_t slots = sm_count;
+    const double item_cost = 2.0;  // in tiles
+    int64_t best_nc = 1;
+    double best = 1e300;
+    const int64_t max_nc = max_chunks(sm_count, n_mtiles, n_ct);
+    for (int64_t nc = 1; nc <= max_nc; ++nc) {
+        const int64_t per = (n_ct + nc - 1) / nc;
+        const int64_t ncs = (n_ct + per - 1) / per;
+        if (ncs != nc) continue;
+        const int64_t waves = (n_mtiles * nc + slots - 1) / slots;
+        const double cost = (double)waves * ((double)per + item_cost);
+        if (cost < best - 1e-9) {
+            best = cost;
+            best_nc = nc;
+        }
+    }
+    *n_chunks = (int)best_nc;
+    *per_chunk = (int)((n_ct + best_nc - 1) / best_nc);
+}
+
+// Several problems in one launch: items of about tiles_per_item column
+// tiles (total tiles / (8 x SMs)), so the persistent CTAs stay balanced.
+void choose_chunks_shared(int sm_count, int64_t n_mtiles, int64_t n_ct, double tiles_per_item,
+                          int* n_chunks, int* per_chunk)
+{
+    int64_t per = (int64_t)(tiles_per_item + 0.5);
+    if (per < 1) per = 1;
+    if (per > n_ct) per = n_ct;
+    int64_t nc = (n_ct + per - 1) / per;
+    const int64_t cap = max_chunks(sm_count, n_mtiles, n_ct);
+    if (nc > cap) nc = cap;
+    per = (n_ct + nc - 1) / nc;
+    nc = (n_ct + per - 1) / per;
+    *n_chunks = (int)nc;
+    *per_chunk = (int)per;
+}
+
+}  // namespace
+
+int positions_per_axis(int N, int B, int L) { return (N >= 2 * B) ? (N - 2 * B) / L + 1 : 0; }
+
+int validate_params(const fic_params* p, int N, int* n_levels)
+{
+    if (!p) return FIC_EINVAL;
+    if (N <= 0 || N > 65535) return FIC_EINVAL;
+    if (!valid_side(p->B_max) || !valid_side(p->B_min) || p->B_min > p->B_max) return FIC_EINVAL;
+    if (N % p->B_max) return FIC_EINVAL;
+    if (p->L < 1) return FIC_EINVAL;
+    if (!(p->err_tol >= 0.0 && p->err_tol <= 255.0)) return FIC_EINVAL;
+    if (p->engine != FIC_ENGINE_TENSOR && p->engine != FIC_ENGINE_PLAIN) return FIC_EINVAL;
+    if (p->reserved != 0) return FIC_EINVAL;
+    const int nl = ilog2i(p->B_max) - ilog2i(p->B_min) + 1;
+    if (nl > FIC_MAX_LEVELS) return FIC_EINVAL;
+    for (int l = 0; l < nl; ++l) {
+        const fic_sset& s = p->S_sets[l];
+        // S = p/q in [0, 1] (Sec. 2); q <= 256 keeps every score term in int64
+        if (s.n_s < 1 || s.n_s > FIC_MAX_S || s.q < 1 || s.q > 256) return FIC_EINVAL;
+        for (int i = 0; i < s.n_s; ++i)
+            if (s.p[i] < 0 || s.p[i] > s.q) return FIC_EINVAL;
+    }
+    *n_levels = nl;
+    return FIC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Engine
+// ---------------------------------------------------------------------------
+Engine::~Engine()
+{
+    for (auto& w : work_) w->release();
+    entT_.release();
+    scal_.release();
+    for (auto& b : probs_) b.release();
+    if (host_scal_) cudaFreeHost(host_scal_);
+}
+
+int Engine::init(cudaStream_t s)
+{
+    if (ready_) return FIC_OK;
+    int dev = 0;
+    FIC_TRY(cudaGetDevice(&dev));
+    FIC_TRY(cudaDeviceGetAttribute(&sm_count_, cudaDevAttrMultiProcessorCount, dev));
+    constexpr int kEntTable = 4097;  // q log2 q for q = 0 .. 4096
+    FIC_TRY(entT_.ensure(sizeof(double) * kEntTable));
+    FIC_TRY(launch_entropy_table(entT_.as<double>(), kEntTable, s));
+    FIC_TRY(cudaStreamSynchronize(s));
+    ready_ = true;
+    return FIC_OK;
+}
+
+int Engine::ensure_slots(int n)
+{
+    if (n > scal_cap_) {
+        int cap = scal_cap_ ? scal_cap_ : 8;
+        while (cap < n) cap *= 2;
+        FIC_TRY(scal_.ensure(sizeof(Scalars) * (size_t)cap));
+        FIC_TRY(cudaMemset(scal_.p, 0, sizeof(Scalars) * (size_t)cap));
+        if (host_scal_) cudaFreeHost(host_scal_);
+        host_scal_ = nullptr;
+        scal_cap_ = 0;
+        FIC_TRY(cudaMallocHost((void**)&host_scal_, sizeof(Scalars) * (size_t)cap));
+        scal_cap_ = cap;
+    }
+    while ((int)work_.size() < n) work_.emplace_back(new ImageWork());
+    return FIC_OK;
+}
+
+int Engine::read_scalars(int n, cudaStream_t s)
+{
+    FIC_TRY(cudaMemcpyAsync(host_scal_, scal_.p, sizeof(Scalars) * (size_t)n,
+                            cudaMemcpyDeviceToHost, s));
+    FIC_TRY(cudaStreamSynchronize(s));
+    return FIC_OK;
+}
+
+int64_t Engine::slot_bytes(int N, const fic_params& p) const
+{
+    int nl = 0;
+    if (validate_params(&p, N, &nl)) return -1;
+    const int64_t cells = (int64_t)(N / p.B_min) * (N / p.B_min);
+    int64_t fixed = (int64_t)N * N * 3                    // image copy + 2x2 sums
+                    + cells * (2 * 16 + 2 * 4 + 3 * 4);   // records x2, act x2, order maps
+    int64_t peak = 0;
+    for (int lvl = 0; lvl < nl; ++lvl) {
+        const StepShape h = step_shape(p, lvl);
+        const int per = positions_per_axis(N, h.B, p.L);
+        const int64_t npos = (int64_t)per * per;
+        const int64_t R = (int64_t)(N / h.B) * (N / h.B);
+        const int64_t cols = round_up(npos > 0 ? npos : 1, kColPad);
+        const int64_t rows = rows_pad_for(h, R);
+        const int64_t n_mtiles = mtiles_for(h, rows);
+        const int64_t nc = max_chunks(sm_count_ > 0 ? sm_count_ : 152, n_mtiles, cols / h.tile_w);
+        const int64_t b = npos * (4 * 3 + 8)                            // flags, pos, pool, H
+                          + cols * (2 * h.K + 4 * h.sp.cw + 8)          // D, cf, ci
+                          + rows * (2 * h.K + 8) + R * (16 + 16 + 8)   // A, gbest, rc, best, split
+                          + R * h.parts_per_chunk * nc * 16;            // partial bests
+        if (b > peak) peak = b;
+    }
+    return fixed + peak + (1 << 20);
+}
+
+int Engine::begin(Job& job, int slot, const uint8_t* img, int N, const fic_params& p,
+                  Launcher& L, cudaStream_t s)
+{
+    int nl = 0;
+    int st = validate_params(&p, N, &nl);
+    if (st) return st;
+    st = ensure_slots(slot + 1);
+    if (st) return st;
+    ImageWork* w = work_[(size_t)slot].get();
+    job = Job();
+    job.slot = slot;
+    job.N = N;
+    job.res.N = N;
+    job.res.B_max = p.B_max;
+    job.res.n_levels = nl;
+    for (int l = 0; l < nl; ++l) job.res.S_sets[l] = p.S_sets[l];
+    job.dimg = img;
+    if (!is_device_ptr(img)) {
+        FIC_TRY(w->img.ensure((size_t)N * N));
+        FIC_TRY(cudaMemcpyAsync(w->img.p, img, (size_t)N * N, cudaMemcpyHostToDevice, s));
+        job.dimg = w->img.as<uint8_t>();
+    }
+    // every record covers >= 1 finest cell
+    job.cells = (int64_t)(N / p.B_min) * (N / p.B_min);
+    FIC_TRY(w->codes_tmp.ensure(sizeof(fic_code) * job.cells));
+    FIC_TRY(w->codes_out.ensure(sizeof(fic_code) * job.cells));
+    FIC_TRY(w->act0.ensure(sizeof(uint32_t) * job.cells));
+    FIC_TRY(w->act1.ensure(sizeof(uint32_t) * job.cells));
+    job.act = w->act0.as<uint32_t>();
+    job.next = w->act1.as<uint32_t>();
+    const int tops = N / p.B_max;
+    job.R = (int64_t)tops * tops;
+    // 2x2 box sums, shared by every step's domain gather
+    FIC_TRY(w->box2.ensure(sizeof(uint16_t) * (size_t)N * N));
+    L.begin(FIC_K_GATHER);
+    FIC_TRY(launch_init_ranges(job.act, tops, p.B_max, s));
+    FIC_TRY(launch_box2(job.dimg, N, w->box2.as<uint16_t>(), s));
+    L.end(2, 0.0, (double)N * N * 3.0);
+    return FIC_OK;
+}
+
+// Pool of one step: entropy flags -> scan -> raster-order list into the
+// slot's pool buffer, its size into the slot's scalars.
+int Engine::launch_pool(Job& j, int B, const fic_params& p, bool want_H, Launcher& L,
+                        cudaStream_t s, double thr)
+{
+    ImageWork* w = work_[(size_t)j.slot].get();
+    Scalars* ds = scal_.as<Scalars>() + j.slot;
+    const int per = positions_per_axis(j.N, B, p.L);
+    const int64_t npos = (int64_t)per * per;
+    FIC_TRY(cudaMemsetAsync(&ds->near, 0, sizeof(unsigned long long), s));
+    if (npos == 0) {
+        FIC_TRY(cudaMemsetAsync(&ds->total, 0, sizeof(uint32_t), s));
+        return FIC_OK;
+    }
+    FIC_TRY(w->flags.ensure(sizeof(uint32_t) * npos));
+    FIC_TRY(w->pos.ensure(sizeof(uint32_t) * npos));
+    FIC_TRY(w->pool.ensure(sizeof(uint32_t) * npos));
+    FIC_TRY(w->scan_tmp.ensure(sizeof(uint32_t) * scan_tmp_words(npos)));
+    if (want_H) FIC_TRY(w->H.ensure(sizeof(double) * npos));
+    L.begin(FIC_K_ENTROPY);
+    FIC_TRY(launch_entropy(j.dimg, j.N, B, p.L, per, thr, entT_.as<double>(),
+                           w->flags.as<uint32_t>(), want_H ? w->H.as<double>() : nullptr,
+                           &ds->near, s));
+    L.end(1, 0.0, (double)npos * (4.0 * B * B + 4.0));
+    L.begin(FIC_K_SCAN);
+    int nl = 0;
+    FIC_TRY(launch_scan(w->flags.as<uint32_t>(), w->pos.as<uint32_t>(), npos,
+                        w->scan_tmp.as<uint32_t>(), &ds->total, s, &nl));
+    FIC_TRY(launch_pool_scatter(w->flags.as<uint32_t>(), w->pos.as<uint32_t>(), npos, per, p.L,
+                                w->pool.as<uint32_t>(), s));
+    L.end(nl + 1, 0.0, (double)npos * 12.0);
+    return FIC_OK;
+}
+
+int Engine::pool_only(int slot, const uint8_t* dimg, int N, int B, int L, double thr,
+                      bool want_H, Launcher& Lk, cudaStream_t s, int64_t* dn, int64_t* near)
+{
+    int st = ensure_slots(slot + 1);
+    if (st) return st;
+    Job j;
+    j.slot = slot;
+    j.dimg = dimg;
+    j.N = N;
+    fic_params p;
+    memset(&p, 0, sizeof(p));
+    p.L = L;
+    st = launch_pool(j, B, p, want_H, Lk, s, thr);
+    if (st) return st;
+    st = read_scalars(slot + 1, s);
+    if (st) return st;
+    const int per = positions_per_axis(N, B, L);
+    *dn = per > 0 ? (int64_t)host_scal_[slot].total : 0;
+    *near = (int64_t)host_scal_[slot].near;
+    return FIC_OK;
+}
+
+int Engine::step(const fic_params& p, const std::vector<Job*>& jobs, Launcher& L,
+                 cudaStream_t s)
+{
+    int nl = 0;
+    int st = validate_params(&p, jobs.empty() ? p.B_max : jobs[0]->N, &nl);
+    if (st) return st;
+    const bool filter = p.entropy_thresh >= 0.0;
+    const int e16 = (int)llround(16.0 * p.err_tol);
+    Scalars* ds = scal_.as<Scalars>();
+    int n_slots = 0;
+    std::vector<Job*> live;
+    for (Job* j : jobs)
+        if (!j->done && j->R > 0) {
+            live.push_back(j);
+            if (j->slot + 1 > n_slots) n_slots = j->slot + 1;
+        }
+    if (live.empty()) return FIC_OK;
+
+    // pools
+    for (Job* j : live) {
+        const int B = p.B_max >> j->lvl;
+        j->per = positions_per_axis(j->N, B, p.L);
+        j->res.n_positions[j->lvl] = (int64_t)j->per * j->per;
+        j->res.ranges[j->lvl] = j->R;
+        j->use_list = filter;
+        if (filter) {
+            st = launch_pool(*j, B, p, false, L, s, p.entropy_thresh);
+            if (st) return st;
+        } else {
+            j->dn = (int64_t)j->per * j->per;
+        }
+    }
+    if (filter) {
+        st = read_scalars(n_slots, s);
+        if (st) return st;
+        for (Job* j : live) {
+            j->dn = j->per > 0 ? (int64_t)host_scal_[j->slot].total : 0;
+            j->res.near_thresh[j->lvl] = (int64_t)host_scal_[j->slot].near;
+        }
+    }
+
+    // domain gathers and range preps
+    double group_tiles[FIC_MAX_LEVELS] = {0, 0, 0, 0};
+    int group_jobs[FIC_MAX_LEVELS] = {0, 0, 0, 0};
+    for (Job* j : live) {
+        const StepShape h = step_shape(p, j->lvl);
+        ImageWork* w = work_[(size_t)j->slot].get();
+        Scalars* d = ds + j->slot;
+        j->res.pool_size[j->lvl] = j->dn;
+        j->res.matches[j->lvl] = 8 * j->R * j->dn;
+        j->cols_pad = round_up(j->dn > 0 ? j->dn : 1, kColPad);
+        j->rows_pad = rows_pad_for(h, j->R);
+        FIC_TRY(w->D.ensure(sizeof(__half) * j->cols_pad * h.K));
+        FIC_TRY(w->cf.ensure(sizeof(float) * j->cols_pad * h.sp.cw));
+        FIC_TRY(w->ci.ensure(sizeof(ColExact) * j->cols_pad));
+        FIC_TRY(w->A.ensure(sizeof(__half) * j->rows_pad * h.K));
+        FIC_TRY(w->rc.ensure(sizeof(RowConst) * (j->rows_pad / 8)));
+        FIC_TRY(w->best.ensure(sizeof(Best) * j->R));
+        FIC_TRY(w->split.ensure(sizeof(uint32_t) * j->R));
+        FIC_TRY(w->split_pos.ensure(sizeof(uint32_t) * j->R));
+        FIC_TRY(w->scan_tmp.ensure(sizeof(uint32_t) * scan_tmp_words(j->R)));
+        const uint32_t* pool_xy = j->use_list ? w->pool.as<uint32_t>() : nullptr;
+        FIC_TRY(cudaMemsetAsync(&d->vd_max, 0, sizeof(unsigned long long), s));
+        FIC_TRY(cudaMemsetAsync(&d->vd_min_key, 0xff, sizeof(unsigned long long), s));
+        L.begin(FIC_K_GATHER);
+        FIC_TRY(launch_gather(w->box2.as<uint16_t>(), j->N, h.B, p.L, j->per, pool_xy, j->dn,
+                              j->cols_pad, h.K, h.sp, w->D.as<__half>(), w->cf.as<float>(),
+                              w->ci.as<ColExact>(), &d->vd_max, &d->vd_min_key, s));
+        L.end(2, 0.0,
+              (double)j->cols_pad * (2.0 * h.K + 4.0 * h.sp.cw + 8.0) +
+                  (double)j->dn * 2.0 * h.n2);
+        L.begin(FIC_K_RANGE_PREP);
+        FIC_TRY(launch_range_prep(j->dimg, j->N, h.B, j->act, (int)j->R, j->rows_pad, h.K, h.sp,
+                                  &d->vd_max, h.iso ? 1 : 0, w->A.as<__half>(),
+                                  w->rc.as<RowConst>(), s));
+        L.end(1, 0.0, (double)j->rows_pad * h.K * 2.0 + (double)j->R * (h.n2 + 20.0));
+        if (j->dn > 0) {
+            group_tiles[j->lvl] +=
+                (double)mtiles_for(h, j->rows_pad) * (double)(j->cols_pad / h.tile_w);
+            group_jobs[j->lvl] += 1;
+        }
+        j->n_chunks = 0;
+        j->n_parts = 0;
+    }
+
+    // one contraction launch per quadtree step present
+    int leaders[FIC_MAX_LEVELS] = {-1, -1, -1, -1};
+    for (int lvl = 0; lvl < nl; ++lvl) {
+        if (group_jobs[lvl] == 0) continue;
+        const StepShape h = step_shape(p, lvl);
+        table_.clear();
+        int64_t items = 0;
+        double flops = 0.0, bytes = 0.0;
+        int64_t matches = 0;
+        for (Job* j : live) {
+            if (j->lvl != lvl || j->dn == 0) continue;
+            ImageWork* w = work_[(size_t)j->slot].get();
+            const int64_t n_mtiles = mtiles_for(h, j->rows_pad);
+            const int64_t n_ct = j->cols_pad / h.tile_w;
+            if (group_jobs[lvl] == 1)
+                choose_chunks_alone(sm_count_, n_mtiles, n_ct, &j->n_chunks, &j->per_chunk);
+            else
+                choose_chunks_shared(sm_count_, n_mtiles, n_ct,
+                                     group_tiles[lvl] / (8.0 * sm_count_), &j->n_chunks,
+                                     &j->per_chunk);
+            j->n_parts = h.parts_per_chunk * j->n_chunks;
+            FIC_TRY(w->part.ensure(sizeof(Best) * j->R * j->n_parts));
+            FIC_TRY(w->gbest.ensure(sizeof(long long) * j->rows_pad));
+            FIC_TRY(cudaMemsetAsync(w->gbest.p, 0x7f, sizeof(long long) * j->rows_pad, s));
+            Problem pr;
+            memset(&pr, 0, sizeof(pr));
+            pr.A = w->A.as<__half>();
+            pr.D = w->D.as<__half>();
+            pr.cf = w->cf.as<float>();
+            pr.ci = w->ci.as<ColExact>();
+            pr.rc = w->rc.as<RowConst>();
+            pr.part = w->part.as<Best>();
+            pr.gbest = w->gbest.as<long long>();
+            pr.rows_pad = j->rows_pad;
+            pr.cols_pad = j->cols_pad;
+            pr.R = (int)j->R;
+            pr.dn = (int)j->dn;
+            pr.n_mtiles = (int)n_mtiles;
+            pr.n_ct = (int)n_ct;
+            pr.n_chunks = j->n_chunks;
+            pr.per_chunk = j->per_chunk;
+            pr.item_start = (int)items;
+            table_.push_back(pr);
+            items += n_mtiles * j->n_chunks;
+            flops += 2.0 * (8.0 * j->R) * (double)j->dn * h.n2;
+            matches += 8 * j->R * j->dn;
+            bytes += (double)j->rows_pad * h.K * 2.0 +
+                     (double)j->cols_pad * (2.0 * h.K + 4.0 * h.sp.cw);
+            if (leaders[lvl] < 0) leaders[lvl] = j->slot;
+        }
+        FIC_TRY(probs_[lvl].ensure(sizeof(Problem) * table_.size()));
+        FIC_TRY(cudaMemcpyAsync(probs_[lvl].p, table_.data(), sizeof(Problem) * table_.size(),
+                                cudaMemcpyHostToDevice, s));
+        ContractArgs a;
+        a.probs = probs_[lvl].as<Problem>();
+        a.n_probs = (int)table_.size();
+        a.n_items = (int)items;
+        a.K = h.K;
+        a.sp = h.sp;
+        a.err = &ds[leaders[lvl]].err;
+        a.grid_ctas = sm_count_;
+        if (p.engine == FIC_ENGINE_TENSOR) {
+            FIC_TRY(cudaMemsetAsync(a.err, 0, 2 * sizeof(int), s));
+            L.begin(FIC_K_CONTRACT_TC);
+            FIC_TRY(h.iso ? launch_contract_tc_iso(a, s) : launch_contract_tc(a, s));
+            L.end(1, flops, bytes, matches);
+        } else {
+            L.begin(FIC_K_CONTRACT_PLAIN);
+            FIC_TRY(launch_contract_plain(a, s));
+            L.end(1, flops, bytes, matches);
+        }
+    }
+
+    // split / requeue
+    for (Job* j : live) {
+        const StepShape h = step_shape(p, j->lvl);
+        ImageWork* w = work_[(size_t)j->slot].get();
+        const uint32_t* pool_xy = j->use_list ? w->pool.as<uint32_t>() : nullptr;
+        const int last = (j->lvl == nl - 1);
+        L.begin(FIC_K_SPLIT);
+        FIC_TRY(launch_split_decide(w->part.as<Best>(), j->n_parts, w->rc.as<RowConst>(),
+                                    (int)j->R, h.n2, h.sp, e16, last, (int)j->dn,
+                                    &ds[j->slot].vd_min_key, w->best.as<Best>(),
+                                    w->split.as<uint32_t>(), s));
+        int nlaunch = 0;
+        FIC_TRY(launch_scan(w->split.as<uint32_t>(), w->split_pos.as<uint32_t>(), j->R,
+                            w->scan_tmp.as<uint32_t>(), &ds[j->slot].total, s, &nlaunch));
+        FIC_TRY(launch_split_scatter(j->act, w->best.as<Best>(), w->split.as<uint32_t>(),
+                                     w->split_pos.as<uint32_t>(), w->rc.as<RowConst>(),
+                                     (int)j->R, h.B, j->lvl, pool_xy, j->per, p.L, (int)j->dn,
+                                     j->next, w->codes_tmp.p, j->n_codes, s));
+        L.end(2 + nlaunch, 0.0, (double)j->R * 64.0);
+    }
+    st = read_scalars(n_slots, s);
+    if (st) return st;
+    if (p.engine == FIC_ENGINE_TENSOR)
+        for (int lvl = 0; lvl < nl; ++lvl)
+            if (leaders[lvl] >= 0 && (host_scal_[leaders[lvl]].err || host_scal_[leaders[lvl]].err2))
+                return FIC_ETIMEOUT;
+    for (Job* j : live) {
+        const int64_t splits = host_scal_[j->slot].total;
+        j->n_codes += j->R - splits;
+        j->R = 4 * splits;
+        std::swap(j->act, j->next);
+        j->lvl += 1;
+        if (j->R == 0 || j->lvl >= nl) j->done = true;
+    }
+    return FIC_OK;
+}
+
+int Engine::finish(Job& j, const fic_params& p, fic_code* dst, int64_t cap, Launcher& L,
+                   cudaStream_t s)
+{
+    ImageWork* w = work_[(size_t)j.slot].get();
+    Scalars* ds = scal_.as<Scalars>() + j.slot;
+    FIC_TRY(w->cellmap.ensure(sizeof(uint32_t) * j.cells));
+    FIC_TRY(w->cellflag.ensure(sizeof(uint32_t) * j.cells));
+    FIC_TRY(w->cellrank.ensure(sizeof(uint32_t) * j.cells));
+    FIC_TRY(w->scan_tmp.ensure(sizeof(uint32_t) * scan_tmp_words(j.cells)));
+    L.begin(FIC_K_ORDER);
+    FIC_TRY(cudaMemsetAsync(w->cellflag.p, 0, sizeof(uint32_t) * j.cells, s));
+    FIC_TRY(launch_order_mark(w->codes_tmp.p, j.n_codes, j.N, p.B_max, p.B_min,
+                              w->cellmap.as<uint32_t>(), w->cellflag.as<uint32_t>(), s));
+    int nl = 0;
+    FIC_TRY(launch_scan(w->cellflag.as<uint32_t>(), w->cellrank.as<uint32_t>(), j.cells,
+                        w->scan_tmp.as<uint32_t>(), &ds->total, s, &nl));
+    FIC_TRY(launch_order_gather(w->codes_tmp.p, w->cellmap.as<uint32_t>(),
+                                w->cellflag.as<uint32_t>(), w->cellrank.as<uint32_t>(), j.cells,
+                                w->codes_out.p, s));
+    L.end(2 + nl, 0.0, (double)j.cells * 16.0 + (double)j.n_codes * 32.0);
+    j.res.n_codes = j.n_codes;
+    if (dst) {
+        j.res.codes = dst;
+        j.res.owns_codes = 0;
+        if (j.n_codes > cap) return FIC_ECAP;
+        FIC_TRY(cudaMemcpyAsync(dst, w->codes_out.p, sizeof(fic_code) * j.n_codes,
+                                cudaMemcpyDefault, s));
+    } else {
+        fic_code* h = (fic_code*)malloc(sizeof(fic_code) * (size_t)(j.n_codes ? j.n_codes : 1));
+        if (!h) return FIC_ENOMEM;
+        j.res.codes = h;
+        j.res.owns_codes = 1;
+        FIC_TRY(cudaMemcpyAsync(h, w->codes_out.p, sizeof(fic_code) * j.n_codes,
+                                cudaMemcpyDeviceToHost, s));
+    }
+    return FIC_OK;
+}
+
+}  // namespace fic

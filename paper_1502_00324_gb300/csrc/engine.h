@@ -1,0 +1,173 @@
+// engine.h -- the quadtree step driver shared by the synchronous entry points
+// (fic_encode*, one engine per device) and the request server (one engine per
+// server).  Internal to libfic.so.
+//
+// An Engine holds device workspaces in slots; a Job is one image in flight,
+// bound to one slot.  step() advances every job it is given by one quadtree
+// step (Sec. 2), each job at its own step: per job the pool (Sec. 3), the
+// domain gather and the range prep; per quadtree step present, ONE grouped
+// contraction + scoring launch over the work items of all its jobs; per job
+// the split decision and requeue.  Host and device meet twice per step()
+// (pool sizes, numbers of splits) whatever the number of jobs.
+#pragma once
+
+#include <cstdint>
+#include <memory>
+#include <mutex>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "fic.h"
+
+namespace fic {
+
+// ---------------------------------------------------------------------------
+// Instrumentation (fic_stats): per-kind launch counts, algorithmic flops and
+// bytes, and (when enabled) device time from events around each stage.
+// ---------------------------------------------------------------------------
+struct StatsState {
+    std::mutex mu;
+    fic_stats st;
+    bool timing = false;
+};
+extern StatsState g_stats;
+
+class Launcher {
+public:
+    explicit Launcher(cudaStream_t s, bool allow_timing = true);
+    ~Launcher() { harvest(); }
+    void begin(int kind);
+    void end(int launches, double flops = 0.0, double bytes = 0.0, int64_t matches = 0);
+    void harvest();
+
+private:
+    struct Pending {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    cudaStream_t s_;
+    bool timing_ = false;
+    int kind_ = FIC_K_MISC;
+    Pending cur_{};
+    std::vector<Pending> pending_;
+};
+
+// Last CUDA error text of this thread (fic_last_error).
+extern thread_local char g_last_error[160];
+int to_status(cudaError_t e);
+
+#define FIC_TRY(expr)                           \
+    do {                                        \
+        cudaError_t e__ = (expr);               \
+        if (e__ != cudaSuccess) {               \
+            return ::fic::to_status(e__);       \
+        }                                       \
+    } while (0)
+
+// Device buffer grown on demand (contents are not kept when it grows).
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    cudaError_t ensure(size_t bytes);
+    void release();
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+// Small device scalars of one slot.
+struct Scalars {
+    uint32_t total;                 // scan total (pool size, splits, records)
+    uint32_t changed;               // decoder: pixels changed in a pass
+    unsigned long long near;        // positions within 1e-9 of the threshold
+    unsigned long long vd_max;      // pool's largest Vd
+    unsigned long long vd_min_key;  // pool's smallest (Vd, index) key
+    int err;                        // contraction error words (err, err + 1)
+    int err2;
+};
+
+// Device workspaces of one slot (kept and grown across jobs).
+struct ImageWork {
+    DevBuf img, box2, flags, pos, scan_tmp, pool, D, cf, ci, A, rc, part, gbest, best, split,
+        split_pos, act0, act1, codes_tmp, codes_out, cellmap, cellflag, cellrank, H;
+    void release();
+};
+
+// One image in flight.
+struct Job {
+    const uint8_t* dimg = nullptr;  // device image (caller's or the slot's copy)
+    int N = 0;
+    int slot = 0;
+    int lvl = 0;                    // next quadtree step to run
+    bool done = false;
+    int64_t R = 0;                  // active ranges at step lvl
+    int64_t n_codes = 0;            // records emitted so far
+    int64_t cells = 0;              // (N / B_min)^2
+    uint32_t* act = nullptr;        // active ranges (x | y << 16)
+    uint32_t* next = nullptr;
+    // per-step values
+    int per = 0;
+    int64_t dn = 0, cols_pad = 0, rows_pad = 0;
+    bool use_list = false;
+    int n_chunks = 0, per_chunk = 0, n_parts = 0;
+    fic_result res{};               // counters; codes set by finish()
+};
+
+int validate_params(const fic_params* p, int N, int* n_levels);
+int positions_per_axis(int N, int B, int L);
+
+class Engine {
+public:
+    Engine() = default;
+    ~Engine();
+    Engine(const Engine&) = delete;
+    Engine& operator=(const Engine&) = delete;
+
+    // Device properties and the entropy table (once, on the current device).
+    int init(cudaStream_t s);
+    int sm_count() const { return sm_count_; }
+    // Slots 0 .. n-1 exist afterwards.
+    int ensure_slots(int n);
+
+    // Binds job to slot, uploads a host image, starts the quadtree: every
+    // B_max block in raster order.  No host synchronisation.
+    int begin(Job& job, int slot, const uint8_t* img, int N, const fic_params& p, Launcher& L,
+              cudaStream_t s);
+    // One quadtree step of every job in jobs (not done); jobs may be at
+    // different steps.  Marks finished jobs done.
+    int step(const fic_params& p, const std::vector<Job*>& jobs, Launcher& L, cudaStream_t s);
+    // Orders a done job's records (raster of top ranges, then TL, TR, BL, BR)
+    // and copies them to dst (host or device, cap records) or, with dst NULL,
+    // to a new host array owned by job.res.  Asynchronous: synchronise s
+    // before reading.
+    int finish(Job& job, const fic_params& p, fic_code* dst, int64_t cap, Launcher& L,
+               cudaStream_t s);
+
+    // Device bytes one slot needs for an N x N image (admission estimate).
+    int64_t slot_bytes(int N, const fic_params& p) const;
+
+    // Pool of one step of one image into slot's work (used by fic_domain_pool).
+    int pool_only(int slot, const uint8_t* dimg, int N, int B, int L, double thr, bool want_H,
+                  Launcher& Lk, cudaStream_t s, int64_t* dn, int64_t* near);
+    ImageWork& work(int slot) { return *work_[(size_t)slot]; }
+    Scalars* dev_scalars() { return scal_.as<Scalars>(); }
+    const Scalars& host_scalars(int slot) const { return host_scal_[slot]; }
+    int read_scalars(int n, cudaStream_t s);
+    const double* entropy_table() const { return entT_.as<double>(); }
+
+private:
+    int launch_pool(Job& j, int B, const fic_params& p, bool want_H, Launcher& L,
+                    cudaStream_t s, double thr);
+    int sm_count_ = 0;
+    bool ready_ = false;
+    DevBuf entT_, scal_, probs_[FIC_MAX_LEVELS];
+    Scalars* host_scal_ = nullptr;
+    int scal_cap_ = 0;
+    std::vector<std::unique_ptr<ImageWork>> work_;
+    std::vector<Problem> table_;
+};
+
+bool is_device_ptr(const void* p);
+
+}  // namespace fic

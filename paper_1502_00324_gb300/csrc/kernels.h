@@ -9,27 +9,16 @@
 
 namespace fic {
 
-// Arguments of one contraction + scoring launch (one quadtree step).
+// Arguments of one contraction + scoring launch (one quadtree step of one or
+// more images).  The problem table lives in device memory.
 struct ContractArgs {
-    const __half* A;      // ranges x isometries, tile layout, rows_pad rows
-    int64_t rows_pad;     // multiple of 128
-    const __half* D;      // pool domains, tile layout, cols_pad rows
-    int64_t cols_pad;     // multiple of kColPad (768)
-    int K;                // 16, 64 or 256
-    const float* cf;      // column filter constants, cols_pad * sp.cw floats
-    const ColExact* ci;   // exact column sums, cols_pad entries
-    const RowConst* rc;   // per active range
-    int R;                // active ranges
-    int dn;               // pool size
-    int n_chunks;         // column chunks per M tile
-    int ctiles_per_chunk; // column tiles per chunk (128 wide for the plain
-                          // engine, 256 wide for the tensor engine)
-    Best* part;           // R * n_chunks partial bests
-    long long* gbest;     // rows_pad best exact keys shared across column chunks
-                          // (filled with kNoCandidate before the launch)
+    const Problem* probs;  // n_probs entries (device)
+    int n_probs;
+    int n_items;           // total work items (sum over problems)
+    int K;                 // 16, 64 or 256
     StepParams sp;
-    int* err;             // device error word
-    int grid_ctas;        // persistent grid size (tensor engine)
+    int* err;              // device error word
+    int grid_ctas;         // persistent grid size (tensor engines)
 };
 
 cudaError_t launch_contract_plain(const ContractArgs& a, cudaStream_t s);
@@ -44,6 +33,7 @@ int contract_tc_iso_ntile(int K);
 size_t contract_tc_smem_bytes(int K);
 int contract_tc_parts_per_chunk();  // partial bests per (range, column chunk)
 int contract_tc_ntile();            // pool columns per tensor-core tile
+constexpr int kPlainNTile = 128;    // pool columns per CUDA-core tile
 
 // Step kernels (stages.cu).
 cudaError_t launch_entropy_table(double* T, int count, cudaStream_t s);
@@ -57,6 +47,8 @@ cudaError_t launch_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* 
                         uint32_t* total, cudaStream_t s, int* launches);
 cudaError_t launch_pool_scatter(const uint32_t* flags, const uint32_t* pos, int64_t n_pos,
                                 int per, int L, uint32_t* pool_xy, cudaStream_t s);
+// Top-level ranges (x | y << 16) of a tops x tops grid of B_max blocks.
+cudaError_t launch_init_ranges(uint32_t* act, int tops, int B_max, cudaStream_t s);
 // 2x2 box sums of the image, pitch N (entries with x or y = N - 1 unused).
 cudaError_t launch_box2(const uint8_t* img, int N, uint16_t* s2, cudaStream_t s);
 cudaError_t launch_gather(const uint16_t* s2img, int N, int B, int L, int per,

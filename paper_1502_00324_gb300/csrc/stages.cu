@@ -258,6 +258,23 @@ __global__ void box2_kernel(const uint8_t* __restrict__ img, int N, uint16_t* __
     s2[(int64_t)y * N + x] = (uint16_t)((int)p0[0] + p0[1] + p0[N] + p0[N + 1]);
 }
 
+// Top-level active ranges: every B_max block in raster order (Sec. 2).
+__global__ void init_ranges_kernel(uint32_t* __restrict__ act, int tops, int B_max)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)tops * tops) return;
+    const uint32_t x = (uint32_t)((i % tops) * B_max), y = (uint32_t)((i / tops) * B_max);
+    act[i] = x | (y << 16);
+}
+
+cudaError_t launch_init_ranges(uint32_t* act, int tops, int B_max, cudaStream_t s)
+{
+    const int64_t n = (int64_t)tops * tops;
+    if (n == 0) return cudaSuccess;
+    init_ranges_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(act, tops, B_max);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_box2(const uint8_t* img, int N, uint16_t* s2, cudaStream_t s)
 {
     if (N < 2) return cudaSuccess;

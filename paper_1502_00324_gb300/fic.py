@@ -57,6 +57,23 @@ class FicParams(C.Structure):
                 ("reserved", C.c_int32)]
 
 
+class FicServerConfig(C.Structure):
+    _fields_ = [("hbm_budget", C.c_int64), ("max_inflight", C.c_int32), ("max_queue", C.c_int32)]
+
+
+class FicTiming(C.Structure):
+    _fields_ = [("submit_ms", C.c_double), ("admit_ms", C.c_double), ("done_ms", C.c_double),
+                ("steps", C.c_int32), ("shared_steps", C.c_int32)]
+
+
+class FicServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("queued", C.c_int64), ("inflight", C.c_int64), ("iterations", C.c_int64),
+                ("contraction_launches", C.c_int64), ("mean_inflight", C.c_double),
+                ("peak_inflight", C.c_int64), ("hbm_in_use", C.c_int64), ("hbm_peak", C.c_int64),
+                ("hbm_budget", C.c_int64), ("matches", C.c_int64), ("busy_ms", C.c_double)]
+
+
 class FicStats(C.Structure):
     _fields_ = [("launches", C.c_int64 * 10), ("ms", C.c_double * 10),
                 ("flops", C.c_double * 10), ("bytes", C.c_double * 10), ("matches", C.c_int64)]
@@ -67,9 +84,10 @@ CODE_DTYPE = np.dtype([("rx", np.uint16), ("ry", np.uint16), ("dx", np.uint16),
                        ("iso", np.uint8), ("s_idx", np.uint8), ("o_q", np.uint8)])
 assert CODE_DTYPE.itemsize == C.sizeof(FicCode) == 16
 
-EXPORTS = ["fic_encode", "fic_encode_ex", "fic_decode", "fic_domain_pool", "fic_result_free",
+EXPORTS = ["fic_encode", "fic_encode_ex", "fic_encode_batch", "fic_decode", "fic_domain_pool", "fic_result_free",
            "fic_strerror", "fic_stats_reset", "fic_stats_read", "fic_version",
-           "fic_domain_pool_noalloc", "fic_last_error"]
+           "fic_domain_pool_noalloc", "fic_last_error", "fic_server_create", "fic_server_submit",
+           "fic_server_poll", "fic_server_stats_read", "fic_server_destroy"]
 
 
 class FicError(RuntimeError):
@@ -96,6 +114,8 @@ def lib():
     L.fic_encode.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
                              C.POINTER(FicSset), C.c_double, C.POINTER(FicResult), vp]
     L.fic_encode_ex.argtypes = [vp, C.POINTER(FicParams), vp, C.c_int64, C.POINTER(FicResult), vp]
+    L.fic_encode_batch.argtypes = [C.c_int, vp, vp, C.POINTER(FicParams), C.POINTER(FicResult),
+                                   vp]
     L.fic_decode.argtypes = [C.POINTER(FicResult), C.c_int, C.c_int, vp, C.POINTER(C.c_int), vp]
     L.fic_domain_pool.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_double,
                                   C.POINTER(C.c_int32), C.c_int64, C.POINTER(C.c_int64),
@@ -111,6 +131,13 @@ def lib():
     L.fic_domain_pool_noalloc.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_double, vp,
                                           C.c_int64, C.POINTER(C.c_int64), vp,
                                           C.POINTER(C.c_int64), vp]
+    L.fic_server_create.argtypes = [C.POINTER(FicParams), C.POINTER(FicServerConfig),
+                                    C.POINTER(vp)]
+    L.fic_server_submit.argtypes = [vp, vp, C.c_int, C.POINTER(C.c_int64)]
+    L.fic_server_poll.argtypes = [vp, C.c_int64, C.c_int, C.POINTER(FicResult),
+                                  C.POINTER(FicTiming)]
+    L.fic_server_stats_read.argtypes = [vp, C.POINTER(FicServerStats)]
+    L.fic_server_destroy.argtypes = [vp]
     _lib = L
     return L
 
@@ -174,12 +201,7 @@ class Encoded:
         return sum(self.matches)
 
 
-def fic_encode_ex(img, N, B_max, B_min, L, entropy_thresh, ssets, err_tol,
-                  engine=ENGINE_TENSOR, stream=None, codes_out=None):
-    """Encode one N x N uint8 image (numpy array, or torch tensor on the host
-    or the GPU).  ``codes_out``: optional torch/numpy buffer of 16-byte
-    records receiving the codes (host or device); otherwise a host array is
-    returned."""
+def make_params(N, B_max, B_min, L, entropy_thresh, ssets, err_tol, engine=ENGINE_TENSOR):
     p = FicParams()
     p.N, p.B_max, p.B_min, p.L = N, B_max, B_min, L
     p.entropy_thresh = float(entropy_thresh)
@@ -187,6 +209,16 @@ def fic_encode_ex(img, N, B_max, B_min, L, entropy_thresh, ssets, err_tol,
     p.S_sets = make_ssets(ssets)
     p.engine = engine
     p.reserved = 0
+    return p
+
+
+def fic_encode_ex(img, N, B_max, B_min, L, entropy_thresh, ssets, err_tol,
+                  engine=ENGINE_TENSOR, stream=None, codes_out=None):
+    """Encode one N x N uint8 image (numpy array, or torch tensor on the host
+    or the GPU).  ``codes_out``: optional torch/numpy buffer of 16-byte
+    records receiving the codes (host or device); otherwise a host array is
+    returned."""
+    p = make_params(N, B_max, B_min, L, entropy_thresh, ssets, err_tol, engine)
     ip, keep = _ptr(img)
     res = FicResult()
     if codes_out is not None:
@@ -199,6 +231,33 @@ def fic_encode_ex(img, N, B_max, B_min, L, entropy_thresh, ssets, err_tol,
     st = lib().fic_encode_ex(ip, C.byref(p), None, 0, C.byref(res), _stream(stream))
     _check(st, "fic_encode_ex")
     return _adopt(res)
+
+
+def fic_encode_batch(imgs, B_max, B_min, L, entropy_thresh, ssets, err_tol,
+                     engine=ENGINE_TENSOR, stream=None):
+    """Encode a list of square uint8 images (numpy arrays or torch tensors,
+    host or GPU, sides may differ) in one batched call; returns one Encoded
+    per image."""
+    n = len(imgs)
+    if n == 0:
+        return []
+    p = make_params(0, B_max, B_min, L, entropy_thresh, ssets, err_tol, engine)
+    ptrs = (C.c_void_p * n)()
+    Ns = (C.c_int * n)()
+    keep = []
+    for i, im in enumerate(imgs):
+        ip, k = _ptr(im)
+        keep.append(k)
+        ptrs[i] = ip
+        Ns[i] = int(im.shape[0])
+    outs = (FicResult * n)()
+    st = lib().fic_encode_batch(n, C.cast(ptrs, C.c_void_p), C.cast(Ns, C.c_void_p), C.byref(p),
+                                outs, _stream(stream))
+    _check(st, "fic_encode_batch")
+    res = []
+    for i in range(n):
+        res.append(_adopt(FicResult.from_buffer_copy(outs[i])))
+    return res
 
 
 def _adopt(res: FicResult) -> Encoded:
@@ -290,3 +349,64 @@ def fic_domain_pool_noalloc(d_img, N, B, L, entropy_thresh, d_pool_xy, d_entropy
                                        ep, C.byref(near), _stream(stream))
     _check(st, "fic_domain_pool_noalloc")
     return int(dn.value), int(near.value)
+
+
+class Server:
+    """Request server of include/fic.h (continuous batching on the current
+    device).  ``submit`` takes a square uint8 image (numpy: copied by the
+    library; torch CUDA tensor: kept referenced here until its ticket is
+    polled) and returns a ticket; ``poll`` returns (Encoded, timing dict),
+    or None while the image is queued or running."""
+
+    def __init__(self, B_max, B_min, L, entropy_thresh, ssets, err_tol, engine=ENGINE_TENSOR,
+                 hbm_budget=0, max_inflight=0, max_queue=0):
+        self._p = make_params(B_max, B_max, B_min, L, entropy_thresh, ssets, err_tol, engine)
+        cfg = FicServerConfig(int(hbm_budget), int(max_inflight), int(max_queue))
+        h = C.c_void_p()
+        _check(lib().fic_server_create(C.byref(self._p), C.byref(cfg), C.byref(h)),
+               "fic_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, img):
+        ip, keep = _ptr(img)
+        t = C.c_int64(0)
+        st = lib().fic_server_submit(self._h, ip, int(img.shape[0]), C.byref(t))
+        _check(st, "fic_server_submit")
+        if not isinstance(img, np.ndarray):
+            self._keep[t.value] = keep
+        return t.value
+
+    def poll(self, ticket, wait_ms=-1):
+        res = FicResult()
+        tm = FicTiming()
+        st = lib().fic_server_poll(self._h, int(ticket), int(wait_ms), C.byref(res), C.byref(tm))
+        if st == FIC_ENOTREADY:
+            return None
+        self._keep.pop(ticket, None)
+        _check(st, "fic_server_poll")
+        timing = {k: getattr(tm, k) for k, _ in FicTiming._fields_}
+        return _adopt(res), timing
+
+    def stats(self):
+        s = FicServerStats()
+        _check(lib().fic_server_stats_read(self._h, C.byref(s)), "fic_server_stats_read")
+        return {k: getattr(s, k) for k, _ in FicServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            lib().fic_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
