@@ -171,6 +171,18 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
+def rank_reduce(times, work, device):
+    """Across the ranks of the default process group: the max of each time
+    and the sum of each work count (replicas: no other exchange)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x) for x in times], dtype=torch.float64, device=device)
+    w = torch.tensor([float(x) for x in work], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return t.tolist(), w.tolist()
+
+
 def run_gpu(args):
     import torch
     import paper_1502_00324_gb300 as pkg
@@ -264,16 +276,9 @@ def run_gpu(args):
         e2e_s = time.perf_counter() - t0
 
     # max over ranks of the times; sum of work
-    vals = torch.tensor([ms_t, float(m_t), e2e_s, float(e2e_m), ms_p, float(m_p)],
-                        dtype=torch.float64, device=dev)
     if world > 1:
-        import torch.distributed as dist
-        mx = vals.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = vals.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        ms_t, e2e_s, ms_p = mx[0].item(), mx[2].item(), mx[4].item()
-        m_t, e2e_m, m_p = sm[1].item(), sm[3].item(), sm[5].item()
+        (ms_t, e2e_s, ms_p), (m_t, e2e_m, m_p) = rank_reduce([ms_t, e2e_s, ms_p],
+                                                             [m_t, e2e_m, m_p], dev)
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
@@ -435,6 +440,92 @@ def run_batch(args):
     return 0
 
 
+# ---------------------------------------------------------------- serving form
+SERVING_DESC = ("serving: Poisson arrivals (seed 7, mean 200 images/s) of uint8 1/f images "
+                "(alpha 2, seed 700000 + i), side uniform over {256, 512, 1024, 2048}; quadtree "
+                "16->8->4, L=2, entropy > 4.0 bits, S {0.1},{0.2,0.4},{0.3,0.8}, RMS tol 8")
+
+
+def _serving_image(args):
+    side, seed = args
+    return fic_synth.one_over_f(int(side), int(seed), 2.0)
+
+
+def run_serving(args):
+    """Request loop: a feeder thread submits each image at its Poisson arrival
+    time to one fic_server (host images); the main thread polls.  Latency =
+    records on the host - submit, on the server's clock."""
+    import multiprocessing as mp
+    t_arr, sides = fic_synth.poisson_requests(args.requests, seed=7, mean_rate_hz=200.0)
+    jobs = [(int(n), 7 * 100000 + i) for i, n in enumerate(sides)]
+    # images are generated before any GPU work, in spawned workers
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        imgs = pool.map(_serving_image, jobs)
+
+    import torch
+    import paper_1502_00324_gb300 as pkg
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ss = pkg.paper_ssets(16, 4)
+    # warm-up: one image of each side through a throw-away server
+    with pkg.Server(16, 4, 2, 4.0, ss, 8.0) as w:
+        for side in sorted(set(int(n) for n in sides)):
+            w.poll(w.submit(fic_synth.one_over_f(side, 1, 2.0)))
+    srv = pkg.Server(16, 4, 2, 4.0, ss, 8.0)
+    tickets = [None] * len(imgs)
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    t0 = time.perf_counter()
+
+    def feed():
+        for i, im in enumerate(imgs):
+            dt = t0 + float(t_arr[i]) - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            tickets[i] = srv.submit(im)
+
+    th = threading.Thread(target=feed)
+    th.start()
+    results = []
+    for i in range(len(imgs)):
+        while tickets[i] is None:
+            time.sleep(0.0005)
+        results.append(srv.poll(tickets[i], wait_ms=-1))
+    th.join()
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    st = srv.stats()
+    srv.close()
+    lat = np.array([tm["done_ms"] - tm["submit_ms"] for _, tm in results])
+    wait = np.array([tm["admit_ms"] - tm["submit_ms"] for _, tm in results])
+    span_ms = max(tm["done_ms"] for _, tm in results) - min(tm["submit_ms"] for _, tm in results)
+    matches = sum(enc.total_matches for enc, _ in results)
+    by_side = {}
+    for (enc, tm), n in zip(results, sides):
+        by_side.setdefault(int(n), []).append(tm["done_ms"] - tm["submit_ms"])
+    line = {
+        "metric": "p50/p99 encode latency and images/s under a Poisson request stream",
+        "workload": "serving", "value": len(results) / (span_ms / 1e3), "unit": "images/s",
+        "n_gpus": 1, "requests": len(results), "higher_is_better": True,
+        "dtype": "fp16->fp32 (exact int)", "data": "synthetic",
+        "config": {"workload": SERVING_DESC, "arrival_span_s": float(t_arr[-1]),
+                   "sides": {str(k): len(v) for k, v in sorted(by_side.items())},
+                   "server": {"hbm_budget": st["hbm_budget"], "max_inflight": 64}},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
+                       "p99": float(np.percentile(lat, 99)), "max": float(lat.max()),
+                       "mean_queue_wait": float(wait.mean())},
+        "latency_ms_by_side_p50": {str(k): float(np.percentile(v, 50))
+                                   for k, v in sorted(by_side.items())},
+        "gmatch_per_s": matches / (span_ms / 1e3) / 1e9,
+        "server": {k: st[k] for k in ("iterations", "contraction_launches", "mean_inflight",
+                                      "peak_inflight", "hbm_peak", "busy_ms", "failed")},
+        "offered_load_images_per_s": len(results) / max(float(t_arr[-1]), 1e-9),
+        "wall_s": wall, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -443,8 +534,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--legs", default="tensor,plain,e2e,cpu",
                     help="measurements to run (profiling runs use 'tensor' alone)")
-    ap.add_argument("--workload", default="precision512", choices=["precision512", "batch64"],
-                    help="precision512: the headline line; batch64: the 64-image batching form")
+    ap.add_argument("--workload", default="precision512",
+                    choices=["precision512", "batch64", "serving"],
+                    help="precision512: the headline line; batch64: the 64-image batching "
+                         "form; serving: the request server under a Poisson stream")
+    ap.add_argument("--requests", type=int, default=200, help="serving: number of requests")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -452,6 +546,8 @@ def main():
     __graft_entry__.build()
     if args.workload == "batch64":
         return run_batch(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_gpu(args)
 
 
