@@ -66,12 +66,14 @@ def lib():
         L.or_score.restype = C.c_int64
         L.or_positions_per_axis.argtypes = [C.c_int, C.c_int, C.c_int]
         L.or_pool_build.argtypes = [u8p, C.c_int, C.c_int, C.c_int, C.c_double, C.POINTER(OrPool)]
+        L.or_pool_build_ex.argtypes = [u8p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int64,
+                                       C.POINTER(OrPool)]
         L.or_pool_free.argtypes = [C.POINTER(OrPool)]
         L.or_search_range.argtypes = [u8p, C.c_int, C.c_int, C.c_int, C.POINTER(OrPool),
                                       C.POINTER(OrSset), i64p, i64p, i32p, i32p]
         L.or_search_ranges.argtypes = [u8p, C.c_int, C.c_int64, i32p, i32p, C.POINTER(OrPool),
                                        C.POINTER(OrSset), C.c_int, i64p, i64p, i32p, i32p]
-        L.or_encode.argtypes = [u8p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
+        L.or_encode.argtypes = [u8p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int64,
                                 C.POINTER(OrSset), C.c_double, C.c_int, C.POINTER(OrCode),
                                 C.c_int64, i64p, C.POINTER(OrStats)]
         L.or_decode.argtypes = [C.POINTER(OrCode), C.c_int64, C.POINTER(OrSset), C.c_int,
@@ -136,13 +138,15 @@ def positions_per_axis(N, B, L):
 
 
 class Pool:
-    """A step's domain pool (positions in raster order and decimated blocks)."""
+    """A step's domain pool (positions in raster order and decimated blocks).
+    ``dn_top`` > 0: the dn_top highest-entropy positions (ties in raster
+    order) instead of the threshold rule."""
 
-    def __init__(self, img, B, L, thr):
+    def __init__(self, img, B, L, thr, dn_top=0):
         self._img, ap = _u8(img)
         self.N = self._img.shape[0]
         self._p = OrPool()
-        rc = lib().or_pool_build(ap, self.N, B, L, thr, C.byref(self._p))
+        rc = lib().or_pool_build_ex(ap, self.N, B, L, thr, int(dn_top), C.byref(self._p))
         if rc:
             raise MemoryError("oracle pool build failed")
         self.B, self.L = B, L
@@ -190,8 +194,9 @@ class Pool:
             pass
 
 
-def encode(img, B_max, B_min, L, entropy_thresh, ssets, err_tol, nthreads=0):
-    """Full oracle encode.  Returns (codes structured array, stats dict)."""
+def encode(img, B_max, B_min, L, entropy_thresh, ssets, err_tol, nthreads=0, pool_dn=0):
+    """Full oracle encode.  Returns (codes structured array, stats dict).
+    ``pool_dn`` > 0 selects the top-DN pool rule at every step."""
     a, ap = _u8(img)
     N = a.shape[0]
     ss = make_ssets(ssets)
@@ -200,7 +205,8 @@ def encode(img, B_max, B_min, L, entropy_thresh, ssets, err_tol, nthreads=0):
     cap = 1024
     while True:
         buf = (OrCode * cap)()
-        rc = lib().or_encode(ap, N, B_max, B_min, L, entropy_thresh, ss, err_tol, nthreads,
+        rc = lib().or_encode(ap, N, B_max, B_min, L, entropy_thresh, int(pool_dn), ss, err_tol,
+                             nthreads,
                              buf, cap, C.byref(n_out), C.byref(st))
         if rc == -2:
             cap = int(n_out.value)

@@ -16,7 +16,8 @@
  *   Eq. 1     E(R,D) = sum_i (S d_i + O - r_i)^2.
  *   Eq. 3     O = mean(R) - S mean(D)   (least-squares optimal offset).
  *   Eq. 5-6   block entropy from grey-level counts (here in bits).
- *   Sec. 3    domain pool = domains with entropy greater than a threshold.
+ *   Sec. 3    domain pool = domains with entropy greater than a threshold;
+ *   Sec. 4    or the DN domains of highest entropy (the experiments' pools).
  *   Sec. 3.2  predefined contrast factors S per step instead of a search.
  *   Sec. 2    quadtree steps: a range whose error exceeds the step threshold
  *             splits into four; the last step stores its best mapping anyway.
@@ -35,6 +36,9 @@
  *     level (e16 = round(16 tol));
  *   - the stored offset is the range mean quantised to 7 bits,
  *     o_q = min(127, floor(sum(r) / (2n))), decoded as 2 o_q + 1;
+ *   - entropy is summed in ascending order of the grey-level counts, so
+ *     equal count multisets give identical values; the top-DN pool compares
+ *     entropies rounded to 2^-20 bit and takes equal ones in raster order;
  *   - entropy threshold < 0 admits every domain; an empty pool at a
  *     non-final step splits every range, at the final step it stores a
  *     mean-only record (pool index 0xFFFFFFFF);
@@ -151,11 +155,21 @@ double or_entropy_bits(const uint8_t* img, int N, int x, int y, int size)
     for (int i = 0; i < size; ++i)
         for (int j = 0; j < size; ++j)
             count[img[(y + i) * N + x + j]] += 1;
-    double total = (double)size * (double)size;
-    double h = 0.0;
+    /* The non-zero counts in ascending order: the sum then depends only on
+     * the multiset of counts, so blocks whose histograms are permutations
+     * of each other (equal entropy) get bit-identical values. */
+    int64_t c[256];
+    int m = 0;
     for (int g = 0; g < 256; ++g) {
         if (count[g] == 0) continue;
-        double p = (double)count[g] / total;
+        int k = m++;
+        while (k > 0 && c[k - 1] > count[g]) { c[k] = c[k - 1]; --k; }
+        c[k] = count[g];
+    }
+    double total = (double)size * (double)size;
+    double h = 0.0;
+    for (int k = 0; k < m; ++k) {
+        double p = (double)c[k] / total;
         h -= p * log2(p);
     }
     return h;
@@ -214,7 +228,35 @@ int or_positions_per_axis(int N, int B, int L)
     return (N - 2 * B) / L + 1;
 }
 
-int or_pool_build(const uint8_t* img, int N, int B, int L, double thr, or_pool* pl)
+/* Top-DN ranking key: entropy rounded to a multiple of 2^-20 bit (half
+ * up), larger first; equal rounded entropies in raster order.  Rounding to
+ * nearest keeps the many exactly dyadic entropies (all counts powers of
+ * two) at the centre of their step, far from any rounding boundary. */
+typedef struct { int64_t hq; int64_t i; } or_rank;
+
+#define OR_HQ_SCALE 1048576.0  /* 2^20 */
+
+static int cmp_rank(const void* a, const void* b)
+{
+    const or_rank* u = (const or_rank*)a;
+    const or_rank* v = (const or_rank*)b;
+    if (u->hq != v->hq) return u->hq > v->hq ? -1 : 1;
+    return (u->i > v->i) - (u->i < v->i);
+}
+
+/* Pool rules (Sec. 3, Sec. 3.2.1, Sec. 4):
+ *   dn_top <= 0: every position whose entropy is greater than thr (thr < 0
+ *                admits all);
+ *   dn_top > 0:  the dn_top positions of highest entropy ("we choose blocks
+ *                with the highest entropy"), entropies compared at 2^-20 bit
+ *                (floor(H 2^20 + 1/2)), equal ones taken in raster order;
+ *                near_thresh then counts positions of the boundary value
+ *                (+-1) whose H 2^20 + 1/2 lies within 1e-6 of an integer,
+ *                where rounding could move them across a step.
+ * Either way the admitted positions are listed in raster order and the list
+ * index is the domain address (Sec. 3.3). */
+int or_pool_build_ex(const uint8_t* img, int N, int B, int L, double thr, int64_t dn_top,
+                     or_pool* pl)
 {
     memset(pl, 0, sizeof(*pl));
     int per = or_positions_per_axis(N, B, L);
@@ -223,22 +265,51 @@ int or_pool_build(const uint8_t* img, int N, int B, int L, double thr, or_pool* 
     pl->x = (int32_t*)malloc(sizeof(int32_t) * (size_t)(pl->n_pos ? pl->n_pos : 1));
     pl->y = (int32_t*)malloc(sizeof(int32_t) * (size_t)(pl->n_pos ? pl->n_pos : 1));
     if (!pl->x || !pl->y) return -1;
-    /* positions in raster order (y first, then x); admit iff H > thr. */
-    for (int iy = 0; iy < per; ++iy)
-        for (int ix = 0; ix < per; ++ix) {
-            int x = ix * L, y = iy * L;
-            int admit = 1;
-            if (thr >= 0.0) {
-                double h = or_entropy_bits(img, N, x, y, 2 * B);
-                if (fabs(h - thr) < 1e-9) pl->near_thresh += 1;
-                admit = h > thr;
-            }
-            if (admit) {
-                pl->x[pl->dn] = x;
-                pl->y[pl->dn] = y;
-                pl->dn += 1;
+    char* admit = (char*)calloc((size_t)(pl->n_pos ? pl->n_pos : 1), 1);
+    if (!admit) return -1;
+    if (dn_top > 0) {
+        or_rank* r = (or_rank*)malloc(sizeof(or_rank) * (size_t)(pl->n_pos ? pl->n_pos : 1));
+        if (!r) { free(admit); return -1; }
+        double* hx = (double*)malloc(sizeof(double) * (size_t)(pl->n_pos ? pl->n_pos : 1));
+        if (!hx) { free(r); free(admit); return -1; }
+        for (int64_t i = 0; i < pl->n_pos; ++i) {
+            double h = or_entropy_bits(img, N, (int)(i % per) * L, (int)(i / per) * L, 2 * B);
+            hx[i] = h * OR_HQ_SCALE + 0.5;
+            r[i].hq = (int64_t)floor(hx[i]);
+            r[i].i = i;
+        }
+        qsort(r, (size_t)pl->n_pos, sizeof(or_rank), cmp_rank);
+        int64_t take = dn_top < pl->n_pos ? dn_top : pl->n_pos;
+        for (int64_t k = 0; k < take; ++k) admit[r[k].i] = 1;
+        if (take > 0 && take < pl->n_pos) {
+            int64_t hb = r[take - 1].hq;
+            for (int64_t i = 0; i < pl->n_pos; ++i) {
+                int64_t hq = (int64_t)floor(hx[i]);
+                double fr = hx[i] - floor(hx[i]);
+                if (hq >= hb - 1 && hq <= hb + 1 && (fr < 1e-6 || fr > 1.0 - 1e-6))
+                    pl->near_thresh += 1;
             }
         }
+        free(hx);
+        free(r);
+    } else {
+        for (int64_t i = 0; i < pl->n_pos; ++i) {
+            admit[i] = 1;
+            if (thr >= 0.0) {
+                double h = or_entropy_bits(img, N, (int)(i % per) * L, (int)(i / per) * L, 2 * B);
+                if (fabs(h - thr) < 1e-9) pl->near_thresh += 1;
+                admit[i] = h > thr;
+            }
+        }
+    }
+    /* admitted positions in raster order (y first, then x) */
+    for (int64_t i = 0; i < pl->n_pos; ++i)
+        if (admit[i]) {
+            pl->x[pl->dn] = (int32_t)(i % per) * L;
+            pl->y[pl->dn] = (int32_t)(i / per) * L;
+            pl->dn += 1;
+        }
+    free(admit);
     size_t cnt = (size_t)(pl->dn ? pl->dn : 1);
     pl->dsum = (int32_t*)malloc(sizeof(int32_t) * cnt * (size_t)n);
     pl->sum_d = (int64_t*)malloc(sizeof(int64_t) * cnt);
@@ -253,6 +324,11 @@ int or_pool_build(const uint8_t* img, int N, int B, int L, double thr, or_pool* 
         pl->sum_d2[c] = s2;
     }
     return 0;
+}
+
+int or_pool_build(const uint8_t* img, int N, int B, int L, double thr, or_pool* pl)
+{
+    return or_pool_build_ex(img, N, B, L, thr, 0, pl);
 }
 
 /* ------------------------------------------------------------------ */
@@ -412,7 +488,7 @@ typedef struct {
 /* Full encoder.  Returns 0, or -1 on bad arguments / allocation failure,
  * or -2 when cap is too small (n_out then holds the needed count). */
 int or_encode(const uint8_t* img, int N, int B_max, int B_min, int L, double thr,
-              const or_sset* ss, double tol, int nthreads, or_code* out,
+              int64_t pool_dn, const or_sset* ss, double tol, int nthreads, or_code* out,
               int64_t cap, int64_t* n_out, or_stats* st)
 {
     if (N <= 0 || B_max < B_min || B_min < 1 || L < 1 || B_max > 32) return -1;
@@ -430,7 +506,7 @@ int or_encode(const uint8_t* img, int N, int B_max, int B_min, int L, double thr
     or_pool pools[OR_MAX_LEVELS];
     memset(pools, 0, sizeof(pools));
     for (int l = 0; l < n_levels; ++l)
-        if (or_pool_build(img, N, B_max >> l, L, thr, &pools[l])) return -1;
+        if (or_pool_build_ex(img, N, B_max >> l, L, thr, pool_dn, &pools[l])) return -1;
 
     int64_t searched[OR_MAX_LEVELS] = { 0 };
     enc_ctx e = { img, N, n_levels, (int)lround(16.0 * tol), pools, ss, searched };

@@ -85,6 +85,31 @@ def brute_pool(img: np.ndarray, B: int, L: int, thr: float):
     return pos
 
 
+def entropy_quantised(block: np.ndarray, bits: int = 20) -> int:
+    """floor(H 2^bits + 1/2) with H (eq. 5-6, bits) evaluated to 50 digits."""
+    import mpmath
+    mpmath.mp.dps = 50
+    c = np.bincount(block.ravel().astype(np.int64), minlength=256)
+    M = int(block.size)
+    t = mpmath.fsum(int(q) * mpmath.log(int(q), 2) for q in c if q > 1)
+    h = mpmath.log(M, 2) - t / M
+    return int(mpmath.floor(h * 2 ** bits + mpmath.mpf(1) / 2))
+
+
+def brute_top_pool(img: np.ndarray, B: int, L: int, dn: int):
+    """The dn highest-entropy positions (entropy rounded to 2^-20 bit from a
+    50-digit evaluation; equal values in raster order), listed in raster
+    order."""
+    N = img.shape[0]
+    cand = []
+    for y in range(0, N - 2 * B + 1, L):
+        for x in range(0, N - 2 * B + 1, L):
+            cand.append((entropy_quantised(img[y:y + 2 * B, x:x + 2 * B]), len(cand), (x, y)))
+    order = sorted(cand, key=lambda c: (-c[0], c[1]))
+    chosen = sorted(order[:dn], key=lambda c: c[1])
+    return [c[2] for c in chosen]
+
+
 def brute_search(img: np.ndarray, rx: int, ry: int, B: int, pool, sset):
     """Exhaustive search of one range: lexicographic min of
     (16 q^2 n E, pool index, isometry, S index)."""
@@ -105,16 +130,18 @@ def brute_search(img: np.ndarray, rx: int, ry: int, B: int, pool, sset):
     return best
 
 
-def brute_encode(img: np.ndarray, B_max: int, B_min: int, L: int, thr: float, ssets, tol):
+def brute_encode(img: np.ndarray, B_max: int, B_min: int, L: int, thr: float, ssets, tol,
+                 pool_fn=None):
     """Quadtree encoder written from Sec. 2: split while RMS error > tol and the
-    step is not the last; children in TL, TR, BL, BR order."""
+    step is not the last; children in TL, TR, BL, BR order.  pool_fn(B), if
+    given, replaces the threshold pool of side B."""
     N = img.shape[0]
     sides = []
     b = B_max
     while b >= B_min:
         sides.append(b)
         b //= 2
-    pools = [brute_pool(img, s, L, thr) for s in sides]
+    pools = [pool_fn(s) if pool_fn else brute_pool(img, s, L, thr) for s in sides]
     tol_f = Fraction(round(16 * tol), 16)
     out = []
 

@@ -182,6 +182,20 @@ def test_entropy_matches_scipy():
         assert abs(got - brute.entropy_bits_scipy(img[y:y + s, x:x + s])) < 1e-12
 
 
+def test_entropy_depends_only_on_the_count_multiset():
+    """Relabelling the grey levels of a block (a bijection) permutes its
+    histogram; eq. 5-6 is unchanged and the oracle's value is bit-identical
+    (the tie rule of the top-DN pool relies on it)."""
+    rng = np.random.default_rng(12)
+    for s in (4, 8, 16, 32):
+        blk = (rng.integers(0, 7, (s, s)) * 31 + rng.integers(0, 2, (s, s))).astype(np.uint8)
+        perm = rng.permutation(256).astype(np.uint8)
+        h0 = oracle.entropy_bits(blk, 0, 0, s)
+        h1 = oracle.entropy_bits(perm[blk], 0, 0, s)
+        assert h0 == h1
+        assert abs(h0 - brute.entropy_bits_scipy(blk)) < 1e-12
+
+
 # ---------------------------------------------------------------- counts (Sec. 1-3)
 
 def test_worked_example_domain_count():
@@ -221,6 +235,52 @@ def test_pool_matches_brute_force(thr):
         want = brute.brute_pool(img, B, L, thr)
         pl = oracle.Pool(img, B, L, thr)
         assert [tuple(p) for p in pl.positions().tolist()] == want
+
+
+@pytest.mark.parametrize("dn", [1, 32, 64, 144, 256, 10 ** 6])
+def test_top_dn_pool_matches_brute_force(dn):
+    """Top-DN pool (Sec. 4: the DN highest-entropy domains), ties in raster
+    order, listed in raster order; DN above the position count keeps all."""
+    img = fic_synth.one_over_f(48, 9, 1.5)
+    for B, L in [(4, 1), (8, 2), (2, 1)]:
+        pl = oracle.Pool(img, B, L, -1.0, dn_top=dn)
+        assert [tuple(p) for p in pl.positions().tolist()] == brute.brute_top_pool(img, B, L, dn)
+        assert pl.near_thresh == 0
+
+
+def test_top_dn_pool_ties_in_raster_order():
+    """A periodic image (period 8): every 8x8 window at step 2 holds one full
+    period, so all positions tie; the pool is the first DN in raster order.
+    With a noisy patch, higher-entropy windows come first, then the tied
+    periodic ones in raster order."""
+    rng = np.random.default_rng(5)
+    tile = rng.integers(0, 6, (8, 8)).astype(np.uint8) * 40
+    img = np.tile(tile, (6, 6))
+    pl = oracle.Pool(img, 4, 2, -1.0, dn_top=10)
+    per = oracle.positions_per_axis(48, 4, 2)
+    want = [((i % per) * 2, (i // per) * 2) for i in range(10)]
+    assert [tuple(p) for p in pl.positions().tolist()] == want
+    img2 = img.copy()
+    img2[30:46, 30:46] = rng.integers(0, 256, (16, 16))
+    for dn in (5, 40, 100):
+        pl = oracle.Pool(img2, 4, 2, -1.0, dn_top=dn)
+        assert [tuple(p) for p in pl.positions().tolist()] == brute.brute_top_pool(img2, 4, 2, dn)
+
+
+def test_top_dn_encode_matches_brute_force():
+    """Quadtree 8 -> 4 -> 2 with a 32-domain top-entropy pool at every step
+    and the paper's S sets per side (2x2 step: {0.5, 0.9})."""
+    img = fic_synth.one_over_f(32, 21, 1.8)
+    ss = [(10, [2, 4]), (10, [3, 8]), (10, [5, 9])]
+    got, st = oracle.encode(img, 8, 2, 2, -1.0, ss, 24.0, pool_dn=32)
+    assert st["pool_size"] == [32, 32, 32]
+    want = brute.brute_encode(img, 8, 2, 2, -1.0, ss, 24.0,
+                              pool_fn=lambda B: brute.brute_top_pool(img, B, 2, 32))
+    assert len(got) == len(want)
+    for g, w in zip(got, want):
+        for f in ("rx", "ry", "level", "B", "iso", "s_idx", "o_q", "dx", "dy", "pool_idx"):
+            assert int(g[f]) == int(w[f]), (f, g, w)
+    assert len(set(int(v) for v in got["B"])) == 3  # records at all three steps
 
 
 def test_search_matches_brute_force():
