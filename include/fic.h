@@ -127,7 +127,13 @@ typedef struct {
     double err_tol;          /* RMS grey levels, quantised to 1/16          */
     fic_sset S_sets[FIC_MAX_LEVELS]; /* one per step, B_max first          */
     int32_t engine;          /* FIC_ENGINE_*                                */
-    int32_t reserved;        /* must be 0                                   */
+    int32_t pool_dn;         /* 0: threshold pool (entropy > entropy_thresh);
+                                > 0: top-DN pool, the pool_dn positions of
+                                highest entropy [Sec. 3.2.1, Sec. 4], with
+                                entropies rounded to 2^-20 bit and equal
+                                ones taken in raster order (entropy_thresh
+                                ignored); near_thresh then counts positions
+                                whose rounding is ambiguous near the cut   */
 } fic_params;
 
 /* fic_encode -- encode one N x N uint8 image (row-major, pitch N).
@@ -180,13 +186,16 @@ int fic_decode(const fic_result* r, int N, int iters_max, uint8_t* out_img,
 /* fic_domain_pool -- kernels (a) and (b) alone: entropy of every 2B x 2B
  * domain position at step L (eq. 5-6, bits, FP64 from integer counts) and
  * the stable raster-order list of admitted positions (Sec. 3).
+ *   pool_dn   0: admit entropy > entropy_thresh (< 0 admits all); > 0: the
+ *             top-DN rule of fic_params.pool_dn.
  *   pool_xy   host, 2 * cap int32 (x, y pairs); may be NULL with cap 0.
  *   entropy   host, n_positions doubles, may be NULL.
- *   dn, near  host outputs (near: positions with |H - thr| < 1e-9).
+ *   dn, near  host outputs (near: positions with |H - thr| < 1e-9, or with
+ *             an ambiguous rounding near the top-DN cut).
  * Returns FIC_ECAP (with *dn set) when cap < DN. */
 int fic_domain_pool(const uint8_t* img, int N, int B, int L, double entropy_thresh,
-                    int32_t* pool_xy, int64_t cap, int64_t* dn, double* entropy,
-                    int64_t* near, void* stream);
+                    int64_t pool_dn, int32_t* pool_xy, int64_t cap, int64_t* dn,
+                    double* entropy, int64_t* near, void* stream);
 
 /* fic_domain_pool_noalloc -- fic_domain_pool for callers that cannot
  * allocate device memory.  The paper has no counterpart: this entry point

@@ -255,10 +255,11 @@ int fic_decode(const fic_result* r, int N, int iters_max, uint8_t* out_img, int*
 }
 
 int fic_domain_pool(const uint8_t* img, int N, int B, int L, double entropy_thresh,
-                    int32_t* pool_xy, int64_t cap, int64_t* dn, double* entropy, int64_t* near,
-                    void* stream)
+                    int64_t pool_dn, int32_t* pool_xy, int64_t cap, int64_t* dn,
+                    double* entropy, int64_t* near, void* stream)
 {
-    if (!img || !dn || N <= 0 || N > 65535 || !valid_side(B) || L < 1) return FIC_EINVAL;
+    if (!img || !dn || N <= 0 || N > 65535 || !valid_side(B) || L < 1 || pool_dn < 0)
+        return FIC_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     Context* c = nullptr;
     int st = get_context(&c, s);
@@ -279,10 +280,10 @@ int fic_domain_pool(const uint8_t* img, int N, int B, int L, double entropy_thre
     // entropy is evaluated for every position; a negative threshold admits all
     int64_t d = 0, nr = 0;
     st = c->eng.pool_only(0, dimg, N, B, L, entropy_thresh < 0.0 ? -1.0e300 : entropy_thresh,
-                          entropy != nullptr, Lk, s, &d, &nr);
+                          pool_dn, entropy != nullptr, Lk, s, &d, &nr);
     if (st) return st;
     *dn = d;
-    if (near) *near = entropy_thresh < 0.0 ? 0 : nr;
+    if (near) *near = (entropy_thresh < 0.0 && pool_dn == 0) ? 0 : nr;
     if (entropy && npos > 0)
         FIC_TRY(cudaMemcpyAsync(entropy, w.H.p, sizeof(double) * npos, cudaMemcpyDeviceToHost, s));
     if (pool_xy && cap >= d && d > 0) {

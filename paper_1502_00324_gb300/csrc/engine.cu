@@ -107,7 +107,7 @@ void ImageWork::release()
 {
     DevBuf* all[] = {&img, &box2, &flags, &pos, &scan_tmp, &pool, &D, &cf, &ci, &A, &rc, &part,
                      &gbest, &best, &split, &split_pos, &act0, &act1, &codes_tmp, &codes_out,
-                     &cellmap, &cellflag, &cellrank, &H};
+                     &cellmap, &cellflag, &cellrank, &H, &keys, &sel};
     for (DevBuf* b : all) b->release();
 }
 
@@ -253,7 +253,7 @@ int validate_params(const fic_params* p, int N, int* n_levels)
     if (p->L < 1) return FIC_EINVAL;
     if (!(p->err_tol >= 0.0 && p->err_tol <= 255.0)) return FIC_EINVAL;
     if (p->engine != FIC_ENGINE_TENSOR && p->engine != FIC_ENGINE_PLAIN) return FIC_EINVAL;
-    if (p->reserved != 0) return FIC_EINVAL;
+    if (p->pool_dn < 0) return FIC_EINVAL;
     const int nl = ilog2i(p->B_max) - ilog2i(p->B_min) + 1;
     if (nl > FIC_MAX_LEVELS) return FIC_EINVAL;
     for (int l = 0; l < nl; ++l) {
@@ -285,9 +285,8 @@ int Engine::init(cudaStream_t s)
     int dev = 0;
     FIC_TRY(cudaGetDevice(&dev));
     FIC_TRY(cudaDeviceGetAttribute(&sm_count_, cudaDevAttrMultiProcessorCount, dev));
-    constexpr int kEntTable = 4097;  // q log2 q for q = 0 .. 4096
-    FIC_TRY(entT_.ensure(sizeof(double) * kEntTable));
-    FIC_TRY(launch_entropy_table(entT_.as<double>(), kEntTable, s));
+    FIC_TRY(entT_.ensure(sizeof(long long) * kEntTableCount));
+    FIC_TRY(launch_entropy_table(entT_.as<long long>(), kEntTableCount, s));
     FIC_TRY(cudaStreamSynchronize(s));
     ready_ = true;
     return FIC_OK;
@@ -335,7 +334,7 @@ int64_t Engine::slot_bytes(int N, const fic_params& p) const
         const int64_t rows = rows_pad_for(h, R);
         const int64_t n_mtiles = mtiles_for(h, rows);
         const int64_t nc = max_chunks(sm_count_ > 0 ? sm_count_ : 152, n_mtiles, cols / h.tile_w);
-        const int64_t b = npos * (4 * 3 + 8)                            // flags, pos, pool, H
+        const int64_t b = npos * (4 * 3 + 8 + 8)                        // flags, pos, pool, H, keys
                           + cols * (2 * h.K + 4 * h.sp.cw + 8)          // D, cf, ci
                           + rows * (2 * h.K + 8) + R * (16 + 16 + 8)   // A, gbest, rc, best, split
                           + R * h.parts_per_chunk * nc * 16;            // partial bests
@@ -385,14 +384,15 @@ int Engine::begin(Job& job, int slot, const uint8_t* img, int N, const fic_param
     return FIC_OK;
 }
 
-// Pool of one step: entropy flags -> scan -> raster-order list into the
-// slot's pool buffer, its size into the slot's scalars.
-int Engine::launch_pool(Job& j, int B, const fic_params& p, bool want_H, Launcher& L,
-                        cudaStream_t s, double thr)
+// Pool of one step: entropy -> flags (threshold rule, or the top-DN keys and
+// a radix select) -> scan -> raster-order list into the slot's pool buffer,
+// its size into the slot's scalars.
+int Engine::launch_pool(Job& j, int B, int L_step, double thr, int64_t top, bool want_H,
+                        Launcher& L, cudaStream_t s)
 {
     ImageWork* w = work_[(size_t)j.slot].get();
     Scalars* ds = scal_.as<Scalars>() + j.slot;
-    const int per = positions_per_axis(j.N, B, p.L);
+    const int per = positions_per_axis(j.N, B, L_step);
     const int64_t npos = (int64_t)per * per;
     FIC_TRY(cudaMemsetAsync(&ds->near, 0, sizeof(unsigned long long), s));
     if (npos == 0) {
@@ -404,23 +404,36 @@ int Engine::launch_pool(Job& j, int B, const fic_params& p, bool want_H, Launche
     FIC_TRY(w->pool.ensure(sizeof(uint32_t) * npos));
     FIC_TRY(w->scan_tmp.ensure(sizeof(uint32_t) * scan_tmp_words(npos)));
     if (want_H) FIC_TRY(w->H.ensure(sizeof(double) * npos));
+    const bool select = top > 0 && top < npos;
+    if (top > 0) FIC_TRY(w->keys.ensure(sizeof(unsigned long long) * npos));
+    if (select) FIC_TRY(w->sel.ensure(select_state_bytes()));
     L.begin(FIC_K_ENTROPY);
-    FIC_TRY(launch_entropy(j.dimg, j.N, B, p.L, per, thr, entT_.as<double>(),
+    FIC_TRY(launch_entropy(j.dimg, j.N, B, L_step, per, thr, entT_.as<long long>(),
                            w->flags.as<uint32_t>(), want_H ? w->H.as<double>() : nullptr,
-                           &ds->near, s));
-    L.end(1, 0.0, (double)npos * (4.0 * B * B + 4.0));
+                           top > 0 ? w->keys.as<unsigned long long>() : nullptr, &ds->near, s));
+    int nl = 1;
+    if (select) {
+        FIC_TRY(launch_top_select(w->keys.as<unsigned long long>(), npos, top, w->sel.p,
+                                  w->flags.as<uint32_t>(), &ds->near, s, &nl));
+    } else if (top > 0) {
+        // the pool holds every position
+        FIC_TRY(launch_fill_u32(w->flags.as<uint32_t>(), npos, 1u, s));
+        ++nl;
+    }
+    L.end(nl, 0.0, (double)npos * (4.0 * B * B + 4.0));
     L.begin(FIC_K_SCAN);
-    int nl = 0;
+    nl = 0;
     FIC_TRY(launch_scan(w->flags.as<uint32_t>(), w->pos.as<uint32_t>(), npos,
                         w->scan_tmp.as<uint32_t>(), &ds->total, s, &nl));
-    FIC_TRY(launch_pool_scatter(w->flags.as<uint32_t>(), w->pos.as<uint32_t>(), npos, per, p.L,
+    FIC_TRY(launch_pool_scatter(w->flags.as<uint32_t>(), w->pos.as<uint32_t>(), npos, per, L_step,
                                 w->pool.as<uint32_t>(), s));
     L.end(nl + 1, 0.0, (double)npos * 12.0);
     return FIC_OK;
 }
 
 int Engine::pool_only(int slot, const uint8_t* dimg, int N, int B, int L, double thr,
-                      bool want_H, Launcher& Lk, cudaStream_t s, int64_t* dn, int64_t* near)
+                      int64_t top, bool want_H, Launcher& Lk, cudaStream_t s, int64_t* dn,
+                      int64_t* near)
 {
     int st = ensure_slots(slot + 1);
     if (st) return st;
@@ -428,10 +441,7 @@ int Engine::pool_only(int slot, const uint8_t* dimg, int N, int B, int L, double
     j.slot = slot;
     j.dimg = dimg;
     j.N = N;
-    fic_params p;
-    memset(&p, 0, sizeof(p));
-    p.L = L;
-    st = launch_pool(j, B, p, want_H, Lk, s, thr);
+    st = launch_pool(j, B, L, thr, top, want_H, Lk, s);
     if (st) return st;
     st = read_scalars(slot + 1, s);
     if (st) return st;
@@ -459,21 +469,24 @@ int Engine::step(const fic_params& p, const std::vector<Job*>& jobs, Launcher& L
         }
     if (live.empty()) return FIC_OK;
 
-    // pools
+    // pools: the threshold rule needs the pool sizes back before the
+    // gathers; the top-DN pool size is known (near counts are read with the
+    // split counts)
+    const int64_t top = p.pool_dn;
     for (Job* j : live) {
         const int B = p.B_max >> j->lvl;
         j->per = positions_per_axis(j->N, B, p.L);
-        j->res.n_positions[j->lvl] = (int64_t)j->per * j->per;
+        const int64_t npos = (int64_t)j->per * j->per;
+        j->res.n_positions[j->lvl] = npos;
         j->res.ranges[j->lvl] = j->R;
-        j->use_list = filter;
-        if (filter) {
-            st = launch_pool(*j, B, p, false, L, s, p.entropy_thresh);
+        j->use_list = filter || top > 0;
+        if (j->use_list) {
+            st = launch_pool(*j, B, p.L, top > 0 ? -1.0 : p.entropy_thresh, top, false, L, s);
             if (st) return st;
-        } else {
-            j->dn = (int64_t)j->per * j->per;
         }
+        j->dn = top > 0 ? (top < npos ? top : npos) : npos;
     }
-    if (filter) {
+    if (filter && top == 0) {
         st = read_scalars(n_slots, s);
         if (st) return st;
         for (Job* j : live) {
@@ -626,6 +639,7 @@ int Engine::step(const fic_params& p, const std::vector<Job*>& jobs, Launcher& L
             if (leaders[lvl] >= 0 && (host_scal_[leaders[lvl]].err || host_scal_[leaders[lvl]].err2))
                 return FIC_ETIMEOUT;
     for (Job* j : live) {
+        if (top > 0) j->res.near_thresh[j->lvl] = (int64_t)host_scal_[j->slot].near;
         const int64_t splits = host_scal_[j->slot].total;
         j->n_codes += j->R - splits;
         j->R = 4 * splits;

@@ -90,7 +90,7 @@ struct Scalars {
 // Device workspaces of one slot (kept and grown across jobs).
 struct ImageWork {
     DevBuf img, box2, flags, pos, scan_tmp, pool, D, cf, ci, A, rc, part, gbest, best, split,
-        split_pos, act0, act1, codes_tmp, codes_out, cellmap, cellflag, cellrank, H;
+        split_pos, act0, act1, codes_tmp, codes_out, cellmap, cellflag, cellrank, H, keys, sel;
     void release();
 };
 
@@ -147,18 +147,18 @@ public:
     // Device bytes one slot needs for an N x N image (admission estimate).
     int64_t slot_bytes(int N, const fic_params& p) const;
 
-    // Pool of one step of one image into slot's work (used by fic_domain_pool).
-    int pool_only(int slot, const uint8_t* dimg, int N, int B, int L, double thr, bool want_H,
-                  Launcher& Lk, cudaStream_t s, int64_t* dn, int64_t* near);
+    // Pool of one step of one image into slot's work (used by fic_domain_pool):
+    // top > 0 selects the top-DN rule, else the threshold rule.
+    int pool_only(int slot, const uint8_t* dimg, int N, int B, int L, double thr, int64_t top,
+                  bool want_H, Launcher& Lk, cudaStream_t s, int64_t* dn, int64_t* near);
     ImageWork& work(int slot) { return *work_[(size_t)slot]; }
     Scalars* dev_scalars() { return scal_.as<Scalars>(); }
     const Scalars& host_scalars(int slot) const { return host_scal_[slot]; }
     int read_scalars(int n, cudaStream_t s);
-    const double* entropy_table() const { return entT_.as<double>(); }
 
 private:
-    int launch_pool(Job& j, int B, const fic_params& p, bool want_H, Launcher& L,
-                    cudaStream_t s, double thr);
+    int launch_pool(Job& j, int B, int L_step, double thr, int64_t top, bool want_H,
+                    Launcher& L, cudaStream_t s);
     int sm_count_ = 0;
     bool ready_ = false;
     DevBuf entT_, scal_, probs_[FIC_MAX_LEVELS];

@@ -36,10 +36,23 @@ int contract_tc_ntile();            // pool columns per tensor-core tile
 constexpr int kPlainNTile = 128;    // pool columns per CUDA-core tile
 
 // Step kernels (stages.cu).
-cudaError_t launch_entropy_table(double* T, int count, cudaStream_t s);
+// Fixed-point table round(q log2 q 2^49), q = 0 .. count - 1 (count <= 1025).
+constexpr int kEntTableCount = 1025;
+cudaError_t launch_entropy_table(long long* T, int count, cudaStream_t s);
+// Entropy of every 2B x 2B position at step L.  keys == NULL: threshold
+// flags (H > thr) and the near-threshold count; else the top-DN keys (and
+// rounding-ambiguity flags, consumed by launch_top_select).
 cudaError_t launch_entropy(const uint8_t* img, int N, int B, int L, int per, double thr,
-                           const double* T, uint32_t* flags, double* H,
-                           unsigned long long* near, cudaStream_t s);
+                           const long long* T, uint32_t* flags, double* H,
+                           unsigned long long* keys, unsigned long long* near, cudaStream_t s);
+// Admission flags of the k smallest keys (k < n); adds the positions whose
+// rounded entropy is ambiguous near the cut to *near.  state: device
+// scratch of select_state_bytes().
+size_t select_state_bytes();
+cudaError_t launch_top_select(const unsigned long long* keys, int64_t n, int64_t k,
+                              void* state, uint32_t* flags, unsigned long long* near,
+                              cudaStream_t s, int* launches);
+cudaError_t launch_fill_u32(uint32_t* a, int64_t n, uint32_t v, cudaStream_t s);
 // Exclusive scan of n uint32 values; *total receives the sum.  tmp holds at
 // least scan_tmp_words(n) words.
 int64_t scan_tmp_words(int64_t n);

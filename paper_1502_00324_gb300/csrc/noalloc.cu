@@ -7,7 +7,7 @@
 // program that pre-reserves all device memory at start-up.  Such callers
 // pass their own device buffers for the image and the outputs; the
 // intermediate arrays (per-position flags, scan positions, scan tile sums,
-// the q log2 q table, two counters) live in one file-scope static device
+// the fixed-point q log2 q table, two counters) live in one file-scope static device
 // array instead of the library's allocating workspace.
 //
 // Scratch: FIC_NOALLOC_MAX_POSITIONS (2^20) domain positions, about 8.1 MB
@@ -31,7 +31,7 @@ namespace fic {
 namespace {
 
 constexpr int64_t kMaxPos = FIC_NOALLOC_MAX_POSITIONS;
-constexpr int kTableCount = 4097;  // q log2 q for q = 0 .. 4096
+constexpr int kTableCount = kEntTableCount;  // fixed-point q log2 q
 constexpr int64_t kScanWords = (kMaxPos + 4095) / 4096 + 1;
 
 constexpr size_t align256(size_t v) { return (v + 255) / 256 * 256; }
@@ -39,7 +39,7 @@ constexpr size_t kOffFlags = 0;
 constexpr size_t kOffPos = align256(kOffFlags + sizeof(uint32_t) * kMaxPos);
 constexpr size_t kOffScan = align256(kOffPos + sizeof(uint32_t) * kMaxPos);
 constexpr size_t kOffTable = align256(kOffScan + sizeof(uint32_t) * kScanWords);
-constexpr size_t kOffTotal = align256(kOffTable + sizeof(double) * kTableCount);
+constexpr size_t kOffTotal = align256(kOffTable + sizeof(long long) * kTableCount);
 constexpr size_t kOffNear = kOffTotal + 8;
 constexpr size_t kScratchBytes = align256(kOffNear + 8);
 
@@ -78,7 +78,7 @@ int setup(cudaStream_t s, unsigned char** base)
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return FIC_ECUDA;
         unsigned char* b = static_cast<unsigned char*>(p);
-        if (launch_entropy_table(reinterpret_cast<double*>(b + kOffTable), kTableCount, s) !=
+        if (launch_entropy_table(reinterpret_cast<long long*>(b + kOffTable), kTableCount, s) !=
             cudaSuccess)
             return FIC_ECUDA;
         if (cudaStreamSynchronize(s) != cudaSuccess) return FIC_ECUDA;
@@ -114,7 +114,7 @@ extern "C" int fic_domain_pool_noalloc(const uint8_t* d_img, int N, int B, int L
     uint32_t* flags = reinterpret_cast<uint32_t*>(base + kOffFlags);
     uint32_t* pos = reinterpret_cast<uint32_t*>(base + kOffPos);
     uint32_t* scan = reinterpret_cast<uint32_t*>(base + kOffScan);
-    const double* table = reinterpret_cast<const double*>(base + kOffTable);
+    const long long* table = reinterpret_cast<const long long*>(base + kOffTable);
     uint32_t* total = reinterpret_cast<uint32_t*>(base + kOffTotal);
     unsigned long long* nr = reinterpret_cast<unsigned long long*>(base + kOffNear);
 
@@ -123,7 +123,7 @@ extern "C" int fic_domain_pool_noalloc(const uint8_t* d_img, int N, int B, int L
     if (cudaMemsetAsync(nr, 0, sizeof(unsigned long long), s) != cudaSuccess) return FIC_ECUDA;
     if (cudaMemsetAsync(total, 0, sizeof(uint32_t), s) != cudaSuccess) return FIC_ECUDA;
     if (npos > 0) {
-        if (launch_entropy(d_img, N, B, L, per, thr, table, flags, d_entropy, nr, s) !=
+        if (launch_entropy(d_img, N, B, L, per, thr, table, flags, d_entropy, nullptr, nr, s) !=
             cudaSuccess)
             return FIC_ECUDA;
         if (launch_scan(flags, pos, npos, scan, total, s, nullptr) != cudaSuccess)

@@ -47,48 +47,179 @@ __device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }
 // ---------------------------------------------------------------------------
 // Eq. 5-6 entropy, in bits, from integer counts:
 //   H = log2(P) - (1/P) sum_g q_g log2 q_g,  P = 4n pixels of the 2B x 2B block.
-// The per-count terms q log2 q come from a table built with CUDA's log2.
+// The sum runs in fixed point: a table holds round(q log2 q 2^49) as int64
+// (built with CUDA's log2; q <= 1024), so the sum over the bins is exact,
+// independent of order, and equal count multisets give identical H.  The
+// sum of one block is below 1024 * 10 * 2^49 < 2^63.
 // ---------------------------------------------------------------------------
-__global__ void entropy_table_kernel(double* T, int count)
+constexpr double kEntScale = 562949953421312.0;  // 2^49
+
+__global__ void entropy_table_kernel(long long* T, int count)
 {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < count) T[q] = q == 0 ? 0.0 : (double)q * log2((double)q);
+    if (q < count) T[q] = q == 0 ? 0LL : llrint((double)q * log2((double)q) * kEntScale);
 }
 
-// One warp per domain position: a 256-bin histogram in shared memory, then
-// the table sum over bins (lane l takes bins 8l..8l+7 in order; the lane
-// partials are combined by a fixed butterfly and lane 0's value is used).
+// One warp per run of kRun positions along x (one row of positions): the
+// 256-bin histogram of the first window in shared memory, then the window
+// slides by L: the L leftmost columns leave, L new columns enter.  Each count
+// change q -> q +- 1 changes the fixed-point sum by T[q +- 1] - T[q] (exact),
+// so per position the warp only adds its lanes' deltas.
+//   thr mode (keys == NULL): flags[pos] = H > thr; near counts |H - thr| < 1e-9.
+//   top mode (keys != NULL): keys[pos] = (2^24 - 1 - Hq) << 40 | pos with
+//     Hq = floor(H 2^20 + 1/2) (larger entropy, then lower index, first), and
+//     flags[pos] = 1 when H 2^20 + 1/2 is within 1e-6 of an integer (a
+//     rounding step could move the position: counted later near the cut).
+constexpr int kRun = 32;
+
 __global__ void __launch_bounds__(256)
 entropy_kernel(const uint8_t* __restrict__ img, int N, int B, int L, int per, double thr,
-               const double* __restrict__ T, uint32_t* __restrict__ flags,
-               double* __restrict__ Hout, unsigned long long* __restrict__ near)
+               const long long* __restrict__ T, uint32_t* __restrict__ flags,
+               double* __restrict__ Hout, unsigned long long* __restrict__ keys,
+               unsigned long long* __restrict__ near)
 {
     __shared__ unsigned hist[8][256];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t pos = (int64_t)blockIdx.x * 8 + w;
-    const int64_t npos = (int64_t)per * per;
-    if (pos >= npos) return;  // whole warp leaves together
-    const int x = (int)(pos % per) * L, y = (int)(pos / per) * L;
+    const int runs_per_row = (per + kRun - 1) / kRun;
+    const int64_t run = (int64_t)blockIdx.x * 8 + w;
+    if (run >= (int64_t)runs_per_row * per) return;  // whole warp leaves together
+    const int iy = (int)(run / runs_per_row);
+    const int ix0 = (int)(run % runs_per_row) * kRun;
+    const int ix1 = min(per, ix0 + kRun);
     const int S = 2 * B, P = S * S;
+    const int y = iy * L;
+    unsigned* h = hist[w];
 #pragma unroll
-    for (int b = 0; b < 8; ++b) hist[w][lane * 8 + b] = 0;
+    for (int b = 0; b < 8; ++b) h[lane * 8 + b] = 0;
     __syncwarp();
-    for (int t = lane; t < P; t += 32) {
-        const int yy = y + t / S, xx = x + t % S;
-        atomicAdd(&hist[w][img[(int64_t)yy * N + xx]], 1u);
+    long long part = 0;  // this lane's share of sum T[q]
+    {
+        const int x = ix0 * L;
+        for (int t = lane; t < P; t += 32) {
+            const unsigned g = img[(int64_t)(y + t / S) * N + x + t % S];
+            const unsigned q = atomicAdd(&h[g], 1u);
+            part += T[q + 1] - T[q];
+        }
     }
-    __syncwarp();
-    double part = 0.0;
+    const double log2P = (double)ilog2(P);
+    for (int ix = ix0; ix < ix1; ++ix) {
+        if (ix > ix0) {
+            // slide by L: columns x - L .. x - L + mc - 1 leave, x + S - mc ..
+            // x + S - 1 enter, mc = min(L, S)
+            // (L >= S: the whole window is replaced)
+            const int x = ix * L;
+            const int mc = L < S ? L : S;
+            const int m = mc * S;
+            __syncwarp();
+            for (int t = lane; t < m; t += 32) {
+                const int r = t / mc, c = t % mc;
+                const unsigned g = img[(int64_t)(y + r) * N + (x - L) + c];
+                const unsigned q = atomicSub(&h[g], 1u);
+                part += T[q - 1] - T[q];
+            }
+            __syncwarp();
+            for (int t = lane; t < m; t += 32) {
+                const int r = t / mc, c = t % mc;
+                const unsigned g = img[(int64_t)(y + r) * N + (x + S - mc) + c];
+                const unsigned q = atomicAdd(&h[g], 1u);
+                part += T[q + 1] - T[q];
+            }
+        }
+        long long tot = part;
 #pragma unroll
-    for (int b = 0; b < 8; ++b) part += T[hist[w][lane * 8 + b]];
-#pragma unroll
-    for (int m = 16; m >= 1; m >>= 1) part += __shfl_xor_sync(0xffffffffu, part, m);
-    if (lane == 0) {
-        const double H = (double)ilog2(P) - part / (double)P;
-        flags[pos] = H > thr ? 1u : 0u;
-        if (Hout) Hout[pos] = H;
-        if (fabs(H - thr) < 1e-9) atomicAdd(near, 1ull);
+        for (int o = 16; o >= 1; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        if (lane == 0) {
+            const int64_t pos = (int64_t)iy * per + ix;
+            const double H = log2P - (double)tot / kEntScale / (double)P;
+            if (Hout) Hout[pos] = H;
+            if (keys) {
+                const double hx = H * 1048576.0 + 0.5;
+                const double fl = floor(hx);
+                const unsigned long long hq = (unsigned long long)fl;
+                keys[pos] = ((0xFFFFFFull - hq) << 40) | (unsigned long long)pos;
+                flags[pos] = (hx - fl < 1e-6 || hx - fl > 1.0 - 1e-6) ? 1u : 0u;
+            } else {
+                flags[pos] = H > thr ? 1u : 0u;
+                if (fabs(H - thr) < 1e-9) atomicAdd(near, 1ull);
+            }
+        }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Top-DN selection: the k-th smallest of n distinct 64-bit keys by an MSD
+// radix select (8 passes of 8 bits; the state lives on the device, so the
+// passes need no host synchronisation), then the admission flags.
+// ---------------------------------------------------------------------------
+struct SelectState {
+    unsigned long long prefix;  // digits fixed so far (the k-th key at the end)
+    long long k;                // rank still to find among keys with the prefix
+};
+
+__global__ void select_init_kernel(SelectState* st, long long k, unsigned* hist)
+{
+    if (threadIdx.x == 0) {
+        st->prefix = 0;
+        st->k = k;
+    }
+    hist[threadIdx.x] = 0;
+}
+
+__global__ void __launch_bounds__(256)
+select_hist_kernel(const unsigned long long* __restrict__ keys, int64_t n,
+                   const SelectState* __restrict__ st, int shift, unsigned* __restrict__ hist)
+{
+    __shared__ unsigned sh[256];
+    sh[threadIdx.x] = 0;
+    __syncthreads();
+    const unsigned long long pre = st->prefix;
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
+        const unsigned long long key = keys[i];
+        const bool match = shift == 56 || ((key ^ pre) >> (shift + 8)) == 0;
+        if (match) atomicAdd(&sh[(key >> shift) & 0xff], 1u);
+    }
+    __syncthreads();
+    if (sh[threadIdx.x]) atomicAdd(&hist[threadIdx.x], sh[threadIdx.x]);
+}
+
+__global__ void __launch_bounds__(256)
+select_pick_kernel(SelectState* st, int shift, unsigned* hist)
+{
+    __shared__ unsigned c[256];
+    const int d = threadIdx.x;
+    c[d] = hist[d];
+    __syncthreads();
+    if (d == 0) {
+        long long k = st->k, below = 0;
+        int digit = 255;
+        for (int i = 0; i < 256; ++i) {
+            if (below + (long long)c[i] >= k) {
+                digit = i;
+                break;
+            }
+            below += c[i];
+        }
+        st->prefix |= (unsigned long long)digit << shift;
+        st->k = k - below;
+    }
+    __syncthreads();
+    hist[d] = 0;
+}
+
+// flags[i] = keys[i] <= k-th key; near counts the positions whose rounded
+// entropy could move by one step (flag set by the entropy kernel) and whose
+// step is within one of the cut.
+__global__ void select_flags_kernel(const unsigned long long* __restrict__ keys, int64_t n,
+                                    const SelectState* __restrict__ st,
+                                    uint32_t* __restrict__ flags,
+                                    unsigned long long* __restrict__ near)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const unsigned long long key = keys[i];
+    const long long hb = (long long)(st->prefix >> 40), hq = (long long)(key >> 40);
+    if (flags[i] && hq >= hb - 1 && hq <= hb + 1) atomicAdd(near, 1ull);
+    flags[i] = key <= st->prefix ? 1u : 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -219,20 +350,55 @@ __global__ void pool_scatter_kernel(const uint32_t* __restrict__ flags,
     pool_xy[pos[i]] = x | (y << 16);
 }
 
-cudaError_t launch_entropy_table(double* T, int count, cudaStream_t s)
+cudaError_t launch_entropy_table(long long* T, int count, cudaStream_t s)
 {
     entropy_table_kernel<<<(count + 255) / 256, 256, 0, s>>>(T, count);
     return cudaGetLastError();
 }
 
 cudaError_t launch_entropy(const uint8_t* img, int N, int B, int L, int per, double thr,
-                           const double* T, uint32_t* flags, double* H,
-                           unsigned long long* near, cudaStream_t s)
+                           const long long* T, uint32_t* flags, double* H,
+                           unsigned long long* keys, unsigned long long* near, cudaStream_t s)
 {
     const int64_t npos = (int64_t)per * per;
     if (npos == 0) return cudaSuccess;
-    entropy_kernel<<<(unsigned)((npos + 7) / 8), 256, 0, s>>>(img, N, B, L, per, thr, T, flags,
-                                                                H, near);
+    const int64_t runs = (int64_t)per * ((per + kRun - 1) / kRun);
+    entropy_kernel<<<(unsigned)((runs + 7) / 8), 256, 0, s>>>(img, N, B, L, per, thr, T, flags,
+                                                                H, keys, near);
+    return cudaGetLastError();
+}
+
+size_t select_state_bytes() { return sizeof(SelectState) + 256 * sizeof(unsigned); }
+
+__global__ void fill_u32_kernel(uint32_t* __restrict__ a, int64_t n, uint32_t v)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = v;
+}
+
+cudaError_t launch_fill_u32(uint32_t* a, int64_t n, uint32_t v, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    fill_u32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, n, v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_top_select(const unsigned long long* keys, int64_t n, int64_t k,
+                              void* state, uint32_t* flags, unsigned long long* near,
+                              cudaStream_t s, int* launches)
+{
+    SelectState* st = static_cast<SelectState*>(state);
+    unsigned* hist = reinterpret_cast<unsigned*>(st + 1);
+    if (n <= 0) return cudaSuccess;
+    select_init_kernel<<<1, 256, 0, s>>>(st, k, hist);
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 1184) blocks = 1184;
+    for (int shift = 56; shift >= 0; shift -= 8) {
+        select_hist_kernel<<<(unsigned)blocks, 256, 0, s>>>(keys, n, st, shift, hist);
+        select_pick_kernel<<<1, 256, 0, s>>>(st, shift, hist);
+    }
+    select_flags_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(keys, n, st, flags, near);
+    if (launches) *launches += 18;
     return cudaGetLastError();
 }
 

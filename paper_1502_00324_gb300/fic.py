@@ -54,7 +54,7 @@ class FicParams(C.Structure):
     _fields_ = [("N", C.c_int32), ("B_max", C.c_int32), ("B_min", C.c_int32), ("L", C.c_int32),
                 ("entropy_thresh", C.c_double), ("err_tol", C.c_double),
                 ("S_sets", FicSset * MAX_LEVELS), ("engine", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("pool_dn", C.c_int32)]
 
 
 class FicServerConfig(C.Structure):
@@ -117,7 +117,7 @@ def lib():
     L.fic_encode_batch.argtypes = [C.c_int, vp, vp, C.POINTER(FicParams), C.POINTER(FicResult),
                                    vp]
     L.fic_decode.argtypes = [C.POINTER(FicResult), C.c_int, C.c_int, vp, C.POINTER(C.c_int), vp]
-    L.fic_domain_pool.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_double,
+    L.fic_domain_pool.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int64,
                                   C.POINTER(C.c_int32), C.c_int64, C.POINTER(C.c_int64),
                                   C.POINTER(C.c_double), C.POINTER(C.c_int64), vp]
     L.fic_result_free.argtypes = [C.POINTER(FicResult)]
@@ -201,24 +201,27 @@ class Encoded:
         return sum(self.matches)
 
 
-def make_params(N, B_max, B_min, L, entropy_thresh, ssets, err_tol, engine=ENGINE_TENSOR):
+def make_params(N, B_max, B_min, L, entropy_thresh, ssets, err_tol, engine=ENGINE_TENSOR,
+                pool_dn=0):
+    """fic_params; pool_dn > 0 selects the top-DN pool instead of the
+    entropy threshold."""
     p = FicParams()
     p.N, p.B_max, p.B_min, p.L = N, B_max, B_min, L
     p.entropy_thresh = float(entropy_thresh)
     p.err_tol = float(err_tol)
     p.S_sets = make_ssets(ssets)
     p.engine = engine
-    p.reserved = 0
+    p.pool_dn = int(pool_dn)
     return p
 
 
 def fic_encode_ex(img, N, B_max, B_min, L, entropy_thresh, ssets, err_tol,
-                  engine=ENGINE_TENSOR, stream=None, codes_out=None):
+                  engine=ENGINE_TENSOR, stream=None, codes_out=None, pool_dn=0):
     """Encode one N x N uint8 image (numpy array, or torch tensor on the host
     or the GPU).  ``codes_out``: optional torch/numpy buffer of 16-byte
     records receiving the codes (host or device); otherwise a host array is
     returned."""
-    p = make_params(N, B_max, B_min, L, entropy_thresh, ssets, err_tol, engine)
+    p = make_params(N, B_max, B_min, L, entropy_thresh, ssets, err_tol, engine, pool_dn)
     ip, keep = _ptr(img)
     res = FicResult()
     if codes_out is not None:
@@ -234,14 +237,14 @@ def fic_encode_ex(img, N, B_max, B_min, L, entropy_thresh, ssets, err_tol,
 
 
 def fic_encode_batch(imgs, B_max, B_min, L, entropy_thresh, ssets, err_tol,
-                     engine=ENGINE_TENSOR, stream=None):
+                     engine=ENGINE_TENSOR, stream=None, pool_dn=0):
     """Encode a list of square uint8 images (numpy arrays or torch tensors,
     host or GPU, sides may differ) in one batched call; returns one Encoded
     per image."""
     n = len(imgs)
     if n == 0:
         return []
-    p = make_params(0, B_max, B_min, L, entropy_thresh, ssets, err_tol, engine)
+    p = make_params(0, B_max, B_min, L, entropy_thresh, ssets, err_tol, engine, pool_dn)
     ptrs = (C.c_void_p * n)()
     Ns = (C.c_int * n)()
     keep = []
@@ -299,9 +302,9 @@ def fic_decode(enc: Encoded, iters_max=64, out=None, stream=None):
     return out, int(used.value)
 
 
-def fic_domain_pool(img, N, B, L, entropy_thresh, stream=None):
+def fic_domain_pool(img, N, B, L, entropy_thresh, stream=None, pool_dn=0):
     """Kernels (a)+(b) alone: (pool positions (DN, 2), entropy per position,
-    near-threshold count)."""
+    near-threshold count); pool_dn > 0: the top-DN rule."""
     ip, keep = _ptr(img)
     per = (N - 2 * B) // L + 1 if N >= 2 * B else 0
     npos = per * per
@@ -309,7 +312,7 @@ def fic_domain_pool(img, N, B, L, entropy_thresh, stream=None):
     xy = np.empty((max(npos, 1), 2), np.int32)
     dn = C.c_int64(0)
     near = C.c_int64(0)
-    st = lib().fic_domain_pool(ip, N, B, L, float(entropy_thresh),
+    st = lib().fic_domain_pool(ip, N, B, L, float(entropy_thresh), int(pool_dn),
                                xy.ctypes.data_as(C.POINTER(C.c_int32)), npos, C.byref(dn),
                                ent.ctypes.data_as(C.POINTER(C.c_double)), C.byref(near),
                                _stream(stream))
@@ -359,8 +362,9 @@ class Server:
     or None while the image is queued or running."""
 
     def __init__(self, B_max, B_min, L, entropy_thresh, ssets, err_tol, engine=ENGINE_TENSOR,
-                 hbm_budget=0, max_inflight=0, max_queue=0):
-        self._p = make_params(B_max, B_max, B_min, L, entropy_thresh, ssets, err_tol, engine)
+                 hbm_budget=0, max_inflight=0, max_queue=0, pool_dn=0):
+        self._p = make_params(B_max, B_max, B_min, L, entropy_thresh, ssets, err_tol, engine,
+                              pool_dn)
         cfg = FicServerConfig(int(hbm_budget), int(max_inflight), int(max_queue))
         h = C.c_void_p()
         _check(lib().fic_server_create(C.byref(self._p), C.byref(cfg), C.byref(h)),

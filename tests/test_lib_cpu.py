@@ -61,12 +61,13 @@ def test_strerror(fic):
 ])
 def test_bad_arguments_rejected_on_host(fic, bad):
     args = dict(N=64, B_max=16, B_min=4, L=1, thr=-1.0, err_tol=8.0,
-                ssets=[(10, [1]), (10, [2, 4]), (10, [3, 8])], engine=0)
+                ssets=[(10, [1]), (10, [2, 4]), (10, [3, 8])], engine=0, pool_dn=0)
     args.update(bad)
     img = np.zeros((64, 64), np.uint8)
     with pytest.raises(fic.FicError) as e:
         fic.fic_encode_ex(img, args["N"], args["B_max"], args["B_min"], args["L"], args["thr"],
-                          args["ssets"], args["err_tol"], engine=args["engine"])
+                          args["ssets"], args["err_tol"], engine=args["engine"],
+                          pool_dn=args["pool_dn"])
     assert e.value.status == fic.fic.FIC_EINVAL
 
 
