@@ -202,6 +202,11 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
 
     w, img, ss = workload()
+    if args.only_side:
+        # profiling aid: one quadtree step at side B over all (512 / B)^2 ranges
+        lvl = {16: 0, 8: 1, 4: 2}[args.only_side]
+        w = dict(w, B_max=args.only_side, B_min=args.only_side)
+        ss = [ss[lvl]]
     N = img.shape[0]
     dimg = torch.from_numpy(img).to(dev)
     cap = (N // w["B_min"]) ** 2
@@ -302,7 +307,7 @@ def run_gpu(args):
     launches = sum(v["launches"] for k, v in st_t.items() if isinstance(v, dict))
 
     cpu = None
-    if "cpu" in legs:
+    if "cpu" in legs and not args.only_side:
         # oracle rate per step on a bounded sample, weighted by this encode's
         # per-step match counts (the oracle's counts are the same: parity)
         import oracle
@@ -324,7 +329,8 @@ def run_gpu(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_img,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp16->fp32 (exact int)",
         "data": "synthetic (seeded 1/f images, stand-ins for the paper's test images)",
-        "config": config_dict(w, {"parallelism": f"replicas x{world}"}),
+        "config": config_dict(w, {"parallelism": f"replicas x{world}",
+                                  "only_side": args.only_side or None}),
         "ms_per_image": ms_per_img,
         "plain": {"value": gmatch_p, "unit": "Gmatch/s",
                   "ms_per_image": (ms_p / psteps) if m_p else None},
@@ -526,6 +532,64 @@ def run_serving(args):
     return 0
 
 
+# ---------------------------------------------------------------- proposed vs entropy-based
+COMPARE_DESC = ("compare: the 512x512 precision image (1/f texture, alpha 2, seed 2, 16 step "
+                "edges), quadtree 16->8->4->2 (the paper's four steps), L=2, top-DN pools "
+                "DN in {32, 64, 144, 192, 256}, RMS tol 8; proposed = the paper's predefined S "
+                "per step ({0.1}, {0.2,0.4}, {0.3,0.8}, {0.5,0.9}); entropy-based baseline = "
+                "S = k/10, k = 1..10, at every step")
+
+
+def run_compare(args):
+    """Encode time and quality of the proposed method (predefined S per step)
+    against the entropy-based baseline (ten S values per step) on the same
+    top-DN pools (Sec. 4, Tables 2-3, eq. 9)."""
+    import torch
+    import paper_1502_00324_gb300 as pkg
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    img = fic_synth.workload_image("precision512")
+    dimg = torch.from_numpy(img).to(dev)
+    prop = [pkg.PAPER_S[b] for b in (16, 8, 4, 2)]
+    base = [(10, list(range(1, 11)))] * 4
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    rows = []
+    for dn in (32, 64, 144, 192, 256):
+        row = {"pool": dn}
+        for name, ss in (("proposed", prop), ("entropy_based", base)):
+            def enc():
+                return pkg.fic_encode_ex(dimg, 512, 16, 2, 2, -1.0, ss, 8.0, stream=stream,
+                                         pool_dn=dn)
+            for _ in range(args.warmup):
+                enc()
+            ms = []
+            for _ in range(args.steps):
+                flush.fill_(1)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                r = enc()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            rec, _ = pkg.fic_decode(r, iters_max=64)
+            mse = float(np.mean((rec.astype(np.float64) - img) ** 2))
+            row[name] = {"ms": statistics.median(ms), "records": r.n_codes,
+                         "records_per_step": [int((r.codes["level"] == l).sum())
+                                              for l in range(4)],
+                         "psnr_db": 10 * np.log10(255.0 ** 2 / mse) if mse > 0 else None,
+                         "gmatch_per_s": r.total_matches / (statistics.median(ms) / 1e3) / 1e9}
+        row["time_ratio_proposed_over_baseline"] = row["proposed"]["ms"] / row["entropy_based"]["ms"]
+        rows.append(row)
+    line = {"metric": "encode ms, proposed vs entropy-based (ten S values) on top-DN pools",
+            "workload": "compare", "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "dtype": "fp16->fp32 (exact int)",
+            "data": "synthetic", "config": {"workload": COMPARE_DESC}, "rows": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -535,10 +599,12 @@ def main():
     ap.add_argument("--legs", default="tensor,plain,e2e,cpu",
                     help="measurements to run (profiling runs use 'tensor' alone)")
     ap.add_argument("--workload", default="precision512",
-                    choices=["precision512", "batch64", "serving"],
+                    choices=["precision512", "batch64", "serving", "compare"],
                     help="precision512: the headline line; batch64: the 64-image batching "
                          "form; serving: the request server under a Poisson stream")
     ap.add_argument("--requests", type=int, default=200, help="serving: number of requests")
+    ap.add_argument("--only-side", type=int, default=0, choices=[0, 16, 8, 4],
+                    help="profiling aid: encode one quadtree step at this side (all ranges)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -548,6 +614,8 @@ def main():
         return run_batch(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "compare":
+        return run_compare(args)
     return run_gpu(args)
 
 

@@ -92,3 +92,16 @@ def test_top_dn_batch_and_server_match_single(pkg):
         for t, want in zip(ts, alone):
             enc, _ = srv.poll(t)
             np.testing.assert_array_equal(enc.codes, want)
+
+
+def test_ten_value_S_baseline_matches_oracle(pkg):
+    """The entropy-based baseline's search space: S = k/10, k = 1..10, at
+    every step (16 -> 2, top-64 pool); both engines against the oracle."""
+    img = fic_synth.with_step_edges(64, 77, alpha=3.0)
+    ss = [(10, list(range(1, 11)))] * 4
+    want, st = oracle.encode(img, 16, 2, 2, -1.0, ss, 12.0, pool_dn=64)
+    assert sum(st["near_thresh"]) == 0
+    for e in (pkg.ENGINE_TENSOR, pkg.ENGINE_PLAIN):
+        enc = pkg.fic_encode_ex(img, 64, 16, 2, 2, -1.0, ss, 12.0, engine=e, pool_dn=64)
+        assert_same_codes(enc.codes, want, 16, f"k/10 engine {e}")
+    assert (want["s_idx"] >= 2).any()  # S values beyond the paper's pairs are chosen
