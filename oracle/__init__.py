@@ -82,6 +82,13 @@ def lib():
         L.or_psnr.restype = C.c_double
         L.or_address_bits.argtypes = [C.c_int64]
         L.or_max_threads.restype = C.c_int
+        L.or_pack.argtypes = [u8p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int64,
+                              C.POINTER(OrSset), i64p, C.POINTER(OrCode), C.c_int64, u8p,
+                              C.c_int64, i64p]
+        L.or_pack.restype = C.c_int64
+        L.or_unpack.argtypes = [u8p, C.c_int64, C.POINTER(OrCode), C.c_int64, i64p,
+                                C.POINTER(OrSset), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                C.POINTER(C.c_int)]
         _lib = L
     return _lib
 
@@ -247,3 +254,47 @@ def address_bits(dn):
 
 def max_threads():
     return int(lib().or_max_threads())
+
+
+def pack(img, codes, B_max, n_levels, L, entropy_thresh, ssets, searched, pool_dn=0):
+    """The stored stream (Sec. 3.3, Fig. 7, eq. 8) of oracle records:
+    (bytes, payload bits).  searched[l]: ranges searched at step l (steps no
+    range reached carry DN = 0)."""
+    a, ap = _u8(img)
+    codes = np.ascontiguousarray(codes, dtype=CODE_DTYPE)
+    ss = make_ssets(ssets)
+    sr = (C.c_int64 * 4)(*[int(v) for v in list(searched) + [0] * (4 - len(searched))])
+    pb = C.c_int64(0)
+    need = lib().or_pack(ap, a.shape[0], B_max, n_levels, L, float(entropy_thresh), int(pool_dn),
+                         ss, sr, codes.ctypes.data_as(C.POINTER(OrCode)), codes.shape[0], None,
+                         0, C.byref(pb))
+    if need < 0:
+        raise ValueError("oracle pack rejected the arguments")
+    out = np.zeros(need, np.uint8)
+    lib().or_pack(ap, a.shape[0], B_max, n_levels, L, float(entropy_thresh), int(pool_dn), ss, sr,
+                  codes.ctypes.data_as(C.POINTER(OrCode)), codes.shape[0],
+                  out.ctypes.data_as(C.POINTER(C.c_uint8)), need, C.byref(pb))
+    return out.tobytes(), int(pb.value)
+
+
+def unpack(stream):
+    """Records, S sets and geometry from a stream written by pack()."""
+    buf = np.frombuffer(stream, np.uint8).copy()
+    n = C.c_int64(0)
+    ss = (OrSset * MAX_LEVELS)()
+    N, Bm, nl = C.c_int(0), C.c_int(0), C.c_int(0)
+    cap = 1024
+    while True:
+        out = (OrCode * cap)()
+        rc = lib().or_unpack(buf.ctypes.data_as(C.POINTER(C.c_uint8)), buf.size, out, cap,
+                             C.byref(n), ss, C.byref(N), C.byref(Bm), C.byref(nl))
+        if rc == -2:
+            cap = int(n.value)
+            continue
+        if rc:
+            raise ValueError("malformed stream")
+        break
+    k = int(n.value)
+    codes = np.frombuffer(bytearray(out)[: k * CODE_DTYPE.itemsize], dtype=CODE_DTYPE).copy()
+    ssets = [(ss[i].q, [ss[i].p[j] for j in range(ss[i].n_s)]) for i in range(nl.value)]
+    return codes, ssets, int(N.value), int(Bm.value)

@@ -630,3 +630,259 @@ int or_max_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------ */
+/* Sec. 3.3, Fig. 7, eq. 8: the stored bit stream.                    */
+/*                                                                    */
+/* Records are stored in their order (top ranges left->right, top->    */
+/* bottom, then TL, TR, BL, BR), so range positions are implicit.     */
+/* Each record: step (2 bits), range mean (7 bits, o_q), and when the */
+/* step's pool is not empty: isometry (3 bits), domain address        */
+/* (X = ceil(log2 DN) bits, eq. 8) and the S index (ceil(log2 |S|)    */
+/* bits: none for a one-valued set, 1 bit for two values).            */
+/* A decoder also needs each step's domain list (the address indexes  */
+/* it) and the S sets; they go in a byte-aligned header:              */
+/*   "FIC1", u16 N, u8 B_max, u8 steps, u16 L, u8 pool rule (0        */
+/*   threshold, 1 top-DN), u32 records; per step: u8 |S|, u16 q,      */
+/*   |S| x u16 p, u32 DN (0 when no range reached the step), u8 list  */
+/*   form (0: none needed - empty pool or every position; 1: DN       */
+/*   positions (x/L, y/L) of ceil(log2 per) bits each; 2: a bitmap of */
+/*   the per^2 positions, whichever is shorter, 1 on ties), then the  */
+/*   list padded to a byte.  Integers are big-endian; bit fields are  */
+/*   written most significant bit first; the payload is padded to a   */
+/*   byte at the end.                                                 */
+/* ------------------------------------------------------------------ */
+typedef struct { uint8_t* buf; int64_t cap, bit; } or_bitw;
+
+static void bw_put(or_bitw* w, uint64_t v, int nb)
+{
+    for (int i = nb - 1; i >= 0; --i) {
+        if (w->buf && (w->bit >> 3) < w->cap) {
+            uint8_t* b = &w->buf[w->bit >> 3];
+            if ((v >> i) & 1u) *b |= (uint8_t)(0x80u >> (w->bit & 7));
+            else *b &= (uint8_t)~(0x80u >> (w->bit & 7));
+        }
+        w->bit += 1;
+    }
+}
+
+static void bw_align(or_bitw* w)
+{
+    while (w->bit & 7) bw_put(w, 0, 1);
+}
+
+/* Bytes of the stream (written to out when cap is large enough; the return
+ * value is the full size either way), or -1 on bad arguments.  *payload_bits
+ * (may be NULL) receives the bits of the records alone.  The pools are
+ * rebuilt from img with the encoder's rule. */
+int64_t or_pack(const uint8_t* img, int N, int B_max, int n_levels, int L, double thr,
+                int64_t pool_dn, const or_sset* ss, const int64_t* searched,
+                const or_code* codes, int64_t n, uint8_t* out, int64_t cap,
+                int64_t* payload_bits)
+{
+    if (N <= 0 || N > 65535 || n_levels < 1 || n_levels > 4 || L < 1 || L > 65535) return -1;
+    or_bitw w = { out, out ? cap : 0, 0 };
+    bw_put(&w, 'F', 8); bw_put(&w, 'I', 8); bw_put(&w, 'C', 8); bw_put(&w, '1', 8);
+    bw_put(&w, (uint64_t)N, 16);
+    bw_put(&w, (uint64_t)B_max, 8);
+    bw_put(&w, (uint64_t)n_levels, 8);
+    bw_put(&w, (uint64_t)L, 16);
+    bw_put(&w, pool_dn > 0 ? 1u : 0u, 8);
+    bw_put(&w, (uint64_t)n, 32);
+    int64_t dn[4] = { 0, 0, 0, 0 };
+    for (int l = 0; l < n_levels; ++l) {
+        const int B = B_max >> l;
+        bw_put(&w, (uint64_t)ss[l].n_s, 8);
+        bw_put(&w, (uint64_t)ss[l].q, 16);
+        for (int i = 0; i < ss[l].n_s; ++i) bw_put(&w, (uint64_t)ss[l].p[i], 16);
+        or_pool pl;
+        memset(&pl, 0, sizeof(pl));
+        if (searched[l] > 0) {
+            if (or_pool_build_ex(img, N, B, L, thr, pool_dn, &pl)) return -1;
+            dn[l] = pl.dn;
+        }
+        const int per = or_positions_per_axis(N, B, L);
+        const int64_t npos = (int64_t)per * per;
+        bw_put(&w, (uint64_t)dn[l], 32);
+        int form = 0;
+        const int pw = or_address_bits(per);
+        if (dn[l] > 0 && dn[l] < npos) form = (dn[l] * 2 * pw <= npos) ? 1 : 2;
+        bw_put(&w, (uint64_t)form, 8);
+        if (form == 1) {
+            for (int64_t c = 0; c < dn[l]; ++c) {
+                bw_put(&w, (uint64_t)(pl.x[c] / L), pw);
+                bw_put(&w, (uint64_t)(pl.y[c] / L), pw);
+            }
+        } else if (form == 2) {
+            int64_t c = 0;
+            for (int64_t i = 0; i < npos; ++i) {
+                const int x = (int)(i % per) * L, y = (int)(i / per) * L;
+                const int in = c < dn[l] && pl.x[c] == x && pl.y[c] == y;
+                if (in) ++c;
+                bw_put(&w, in ? 1u : 0u, 1);
+            }
+        }
+        bw_align(&w);
+        if (searched[l] > 0) or_pool_free(&pl);
+    }
+    const int64_t head = w.bit;
+    for (int64_t i = 0; i < n; ++i) {
+        const or_code* c = &codes[i];
+        const int l = c->level;
+        if (l < 0 || l >= n_levels) return -1;
+        bw_put(&w, (uint64_t)l, 2);
+        bw_put(&w, (uint64_t)c->o_q, 7);
+        if (dn[l] > 0) {
+            bw_put(&w, (uint64_t)c->iso, 3);
+            bw_put(&w, (uint64_t)c->pool_idx, or_address_bits(dn[l]));
+            bw_put(&w, (uint64_t)c->s_idx, or_address_bits(ss[l].n_s));
+        }
+    }
+    if (payload_bits) *payload_bits = w.bit - head;
+    bw_align(&w);
+    return w.bit >> 3;
+}
+
+typedef struct { const uint8_t* buf; int64_t n, bit; int bad; } or_bitr;
+
+static uint64_t br_get(or_bitr* r, int nb)
+{
+    uint64_t v = 0;
+    for (int i = 0; i < nb; ++i) {
+        if ((r->bit >> 3) >= r->n) { r->bad = 1; return 0; }
+        v = (v << 1) | ((r->buf[r->bit >> 3] >> (7 - (r->bit & 7))) & 1u);
+        r->bit += 1;
+    }
+    return v;
+}
+
+typedef struct {
+    or_bitr* r;
+    int B_max, n_levels, L, N;
+    int64_t dn[4];
+    int per[4];
+    int32_t* lx[4];
+    int32_t* ly[4];
+    const or_sset* ss;
+    or_code* out;
+    int64_t cap, n;
+    uint64_t pending;  /* step of the record read ahead, or ~0 */
+} or_unpack_ctx;
+
+static int unpack_block(or_unpack_ctx* u, int x, int y, int lvl)
+{
+    if (lvl >= u->n_levels) return -1;
+    if (u->pending == ~(uint64_t)0) u->pending = br_get(u->r, 2);
+    if (u->r->bad) return -1;
+    if ((int)u->pending > lvl) {
+        const int h = (u->B_max >> lvl) / 2;
+        if (unpack_block(u, x, y, lvl + 1) || unpack_block(u, x + h, y, lvl + 1) ||
+            unpack_block(u, x, y + h, lvl + 1) || unpack_block(u, x + h, y + h, lvl + 1))
+            return -1;
+        return 0;
+    }
+    if ((int)u->pending != lvl) return -1;
+    u->pending = ~(uint64_t)0;
+    or_code c;
+    memset(&c, 0, sizeof(c));
+    c.rx = x; c.ry = y; c.level = lvl; c.B = u->B_max >> lvl;
+    c.o_q = (int32_t)br_get(u->r, 7);
+    if (u->dn[lvl] > 0) {
+        c.iso = (int32_t)br_get(u->r, 3);
+        c.pool_idx = (uint32_t)br_get(u->r, or_address_bits(u->dn[lvl]));
+        c.s_idx = (int32_t)br_get(u->r, or_address_bits(u->ss[lvl].n_s));
+        if ((int64_t)c.pool_idx >= u->dn[lvl]) return -1;
+        c.dx = u->lx[lvl][c.pool_idx];
+        c.dy = u->ly[lvl][c.pool_idx];
+    } else {
+        c.s_idx = -1;
+        c.pool_idx = 0xFFFFFFFFu;
+    }
+    if (u->r->bad) return -1;
+    if (u->n < u->cap) u->out[u->n] = c;
+    u->n += 1;
+    return 0;
+}
+
+/* Reads a stream written by or_pack.  Returns 0, -1 on a malformed stream,
+ * -2 when cap is too small (*n_out then holds the count).  ss_out receives
+ * the S sets (4 entries), *N_out, *B_max_out, *n_levels_out the geometry. */
+int or_unpack(const uint8_t* in, int64_t nbytes, or_code* out, int64_t cap, int64_t* n_out,
+              or_sset* ss_out, int* N_out, int* B_max_out, int* n_levels_out)
+{
+    or_bitr r = { in, nbytes, 0, 0 };
+    if (br_get(&r, 32) != (((uint64_t)'F' << 24) | ((uint64_t)'I' << 16) | ((uint64_t)'C' << 8) | '1'))
+        return -1;
+    or_unpack_ctx u;
+    memset(&u, 0, sizeof(u));
+    u.r = &r;
+    u.N = (int)br_get(&r, 16);
+    u.B_max = (int)br_get(&r, 8);
+    u.n_levels = (int)br_get(&r, 8);
+    u.L = (int)br_get(&r, 16);
+    (void)br_get(&r, 8);
+    const int64_t n_codes = (int64_t)br_get(&r, 32);
+    if (r.bad || u.n_levels < 1 || u.n_levels > 4 || u.L < 1 || u.B_max < 1 || u.N % u.B_max)
+        return -1;
+    memset(ss_out, 0, sizeof(or_sset) * 4);
+    int rc = 0;
+    for (int l = 0; l < u.n_levels && !rc; ++l) {
+        const int B = u.B_max >> l;
+        ss_out[l].n_s = (int)br_get(&r, 8);
+        ss_out[l].q = (int)br_get(&r, 16);
+        if (ss_out[l].n_s > OR_MAX_S) { rc = -1; break; }
+        for (int i = 0; i < ss_out[l].n_s; ++i) ss_out[l].p[i] = (int)br_get(&r, 16);
+        u.dn[l] = (int64_t)br_get(&r, 32);
+        const int form = (int)br_get(&r, 8);
+        const int per = or_positions_per_axis(u.N, B, u.L);
+        const int64_t npos = (int64_t)per * per;
+        const int pw = or_address_bits(per);
+        u.per[l] = per;
+        if (u.dn[l] > npos) { rc = -1; break; }
+        u.lx[l] = (int32_t*)malloc(sizeof(int32_t) * (size_t)(u.dn[l] ? u.dn[l] : 1));
+        u.ly[l] = (int32_t*)malloc(sizeof(int32_t) * (size_t)(u.dn[l] ? u.dn[l] : 1));
+        if (!u.lx[l] || !u.ly[l]) { rc = -1; break; }
+        if (form == 0) {
+            if (u.dn[l] != 0 && u.dn[l] != npos) { rc = -1; break; }
+            for (int64_t i = 0; i < u.dn[l]; ++i) {
+                u.lx[l][i] = (int32_t)(i % per) * u.L;
+                u.ly[l][i] = (int32_t)(i / per) * u.L;
+            }
+        } else if (form == 1) {
+            for (int64_t i = 0; i < u.dn[l]; ++i) {
+                u.lx[l][i] = (int32_t)br_get(&r, pw) * u.L;
+                u.ly[l][i] = (int32_t)br_get(&r, pw) * u.L;
+            }
+        } else if (form == 2) {
+            int64_t c = 0;
+            for (int64_t i = 0; i < npos; ++i)
+                if (br_get(&r, 1)) {
+                    if (c >= u.dn[l]) { rc = -1; break; }
+                    u.lx[l][c] = (int32_t)(i % per) * u.L;
+                    u.ly[l][c] = (int32_t)(i / per) * u.L;
+                    ++c;
+                }
+            if (!rc && c != u.dn[l]) rc = -1;
+        } else {
+            rc = -1;
+        }
+        while (r.bit & 7) (void)br_get(&r, 1);
+    }
+    if (!rc) {
+        u.ss = ss_out;
+        u.out = out;
+        u.cap = cap;
+        u.pending = ~(uint64_t)0;
+        const int tops = u.N / u.B_max;
+        for (int t = 0; t < tops * tops && !rc; ++t)
+            rc = unpack_block(&u, (t % tops) * u.B_max, (t / tops) * u.B_max, 0);
+        if (!rc && (r.bad || u.n != n_codes)) rc = -1;
+    }
+    for (int l = 0; l < 4; ++l) { free(u.lx[l]); free(u.ly[l]); }
+    *n_out = u.n;
+    *N_out = u.N;
+    *B_max_out = u.B_max;
+    *n_levels_out = u.n_levels;
+    if (rc) return rc;
+    return u.n > cap ? -2 : 0;
+}

@@ -425,3 +425,114 @@ def test_predefined_S_and_steps_golden():
         q, ps = fic_synth.images.PAPER_S[int(side)]
         assert [Fraction(p, q) for p in ps] == [Fraction(v).limit_denominator(100) for v in vals]
     assert GOLD["steps"]["sides"] == [16, 8, 4, 2]
+
+
+# ---------------------------------------------------------------- stored stream (Sec. 3.3, Fig. 7, eq. 8)
+
+def _bits_writer():
+    bits = []
+
+    def put(v, n):
+        for i in range(n - 1, -1, -1):
+            bits.append((int(v) >> i) & 1)
+
+    def align():
+        while len(bits) % 8:
+            bits.append(0)
+
+    def tobytes():
+        align()
+        return bytes(int("".join(map(str, bits[i:i + 8])), 2) for i in range(0, len(bits), 8))
+
+    return bits, put, align, tobytes
+
+
+def _ceil_log2(v):
+    return 0 if v <= 1 else int(math.ceil(math.log2(v)))
+
+
+def _stream_python(img, codes, B_max, n_levels, L, ssets, pools, rule):
+    """The stream written from the format statement alone (independent of
+    the C writer): header, per-step S set and domain list, then records of
+    step 2 bits, mean 7 bits, isometry 3 bits, address ceil(log2 DN) bits,
+    S index ceil(log2 |S|) bits."""
+    bits, put, align, tobytes = _bits_writer()
+    N = img.shape[0]
+    for ch in b"FIC1":
+        put(ch, 8)
+    put(N, 16); put(B_max, 8); put(n_levels, 8); put(L, 16); put(rule, 8); put(len(codes), 32)
+    for l in range(n_levels):
+        q, ps = ssets[l]
+        put(len(ps), 8); put(q, 16)
+        for p in ps:
+            put(p, 16)
+        pool = pools[l]
+        put(len(pool), 32)
+        per = (N - 2 * (B_max >> l)) // L + 1
+        pw = _ceil_log2(per)
+        npos = per * per
+        form = 0 if len(pool) in (0, npos) else (1 if len(pool) * 2 * pw <= npos else 2)
+        put(form, 8)
+        if form == 1:
+            for x, y in pool:
+                put(x // L, pw); put(y // L, pw)
+        elif form == 2:
+            s = set(pool)
+            for i in range(npos):
+                put(1 if ((i % per) * L, (i // per) * L) in s else 0, 1)
+        align()
+    for c in codes:
+        l = int(c["level"])
+        put(l, 2); put(int(c["o_q"]), 7)
+        if pools[l]:
+            put(int(c["iso"]), 3)
+            put(int(c["pool_idx"]), _ceil_log2(len(pools[l])))
+            put(int(c["s_idx"]), _ceil_log2(len(ssets[l][1])))
+    return tobytes()
+
+
+@pytest.mark.parametrize("case", [
+    dict(N=64, B_max=16, n=3, L=2, thr=4.0, dn=0, tol=8.0, seed=5),      # threshold pools
+    dict(N=64, B_max=16, n=3, L=2, thr=-1.0, dn=32, tol=8.0, seed=6),    # top-32 pools
+    dict(N=48, B_max=8, n=3, L=1, thr=-1.0, dn=0, tol=12.0, seed=7),     # full pools
+    dict(N=32, B_max=8, n=3, L=1, thr=4.0, dn=0, tol=2.0, seed=8),       # empty last pool
+])
+def test_stream_roundtrip_and_independent_writer(case):
+    img = fic_synth.with_step_edges(case["N"], case["seed"], alpha=2.5)
+    sides = [case["B_max"] >> l for l in range(case["n"])]
+    S = {16: (10, [1]), 8: (10, [2, 4]), 4: (10, [3, 8]), 2: (10, [5, 9])}
+    ss = [S[b] for b in sides]
+    codes, st = oracle.encode(img, case["B_max"], sides[-1], case["L"], case["thr"], ss,
+                              case["tol"], pool_dn=case["dn"])
+    stream, pbits = oracle.pack(img, codes, case["B_max"], case["n"], case["L"], case["thr"], ss,
+                                st["ranges"], pool_dn=case["dn"])
+    back, ss2, N2, Bm2 = oracle.unpack(stream)
+    assert (N2, Bm2) == (case["N"], case["B_max"]) and ss2 == ss
+    for f in ("rx", "ry", "level", "B", "iso", "s_idx", "o_q", "dx", "dy", "pool_idx"):
+        np.testing.assert_array_equal(back[f], codes[f], err_msg=f)
+    pools = []
+    for l, B in enumerate(sides):
+        if st["ranges"][l] == 0:
+            pools.append([])
+        elif case["dn"]:
+            pools.append(brute.brute_top_pool(img, B, case["L"], case["dn"]))
+        else:
+            pools.append(brute.brute_pool(img, B, case["L"], case["thr"]))
+    assert stream == _stream_python(img, codes, case["B_max"], case["n"], case["L"], ss, pools,
+                                    1 if case["dn"] else 0)
+    # record bits (Fig. 7, eq. 8): step 2 + mean 7 + [pool] (isometry 3 + address + S index)
+    want = sum(9 + ((3 + _ceil_log2(len(pools[int(c["level"])])) +
+                     _ceil_log2(len(ss[int(c["level"])][1]))) if pools[int(c["level"])] else 0)
+               for c in codes)
+    assert pbits == want
+
+
+def test_stream_field_widths_follow_fig7():
+    g = GOLD["record_fields_bits"]
+    # S field: none for the one-valued step-1 set, one bit for the two-valued sets
+    by_side = GOLD["predefined_S"]["by_side"]
+    assert [_ceil_log2(len(by_side[str(b)])) for b in (16, 8, 4, 2)] == g["s_bits_by_step"]
+    assert _ceil_log2(4) == g["step"] and _ceil_log2(8) == g["isometry"]
+    # the address field is eq. 8's X = ceil(log2 DN)
+    for dn, bits in GOLD["address_bits"]["cases"]:
+        assert _ceil_log2(dn) == bits
