@@ -221,6 +221,28 @@ int fic_domain_pool_noalloc(const uint8_t* d_img, int N, int B, int L,
                             double entropy_thresh, uint32_t* d_pool_xy, int64_t cap,
                             int64_t* dn, double* d_entropy, int64_t* near, void* stream);
 
+/* fic_pack -- the stored stream of an encode [Sec. 3.3, Fig. 7, eq. 8].
+ * Records in their stored order (ranges implicit), each: step (2 bits),
+ * range mean o_q (7 bits), and when the step's pool is not empty the
+ * isometry (3 bits), the domain address (X = ceil(log2 DN) bits, eq. 8) and
+ * the S index (ceil(log2 |S|) bits: none for a one-valued set).  Before the
+ * records, a byte-aligned header carries what a decoder needs: "FIC1", u16
+ * N, u8 B_max, u8 steps, u16 L, u8 pool rule (0 threshold, 1 top-DN), u32
+ * records; per step u8 |S|, u16 q, |S| x u16 p, u32 DN (0 when no range
+ * reached the step), u8 list form and the step's domain list (form 0: none
+ * needed, empty pool or every position; 1: DN positions (x/L, y/L) of
+ * ceil(log2 per) bits each; 2: a bitmap of the per^2 positions, whichever
+ * is shorter, 1 on ties), padded to a byte.  Integers big-endian, fields
+ * most significant bit first, the records padded to a byte at the end.
+ *   img    the encoded image (host or device), to rebuild the domain lists
+ *          with the encode's pool rule; p the encode's parameters (p->N is
+ *          taken from r->N); r the result (codes host or device).
+ *   out    host buffer of cap bytes, or NULL with cap 0 for the size only.
+ *   n_bytes, payload_bits  host outputs (stream bytes; record bits alone).
+ * Returns FIC_ECAP (with *n_bytes set) when cap < *n_bytes. */
+int fic_pack(const uint8_t* img, const fic_params* p, const fic_result* r, uint8_t* out,
+             int64_t cap, int64_t* n_bytes, int64_t* payload_bits, void* stream);
+
 /* ------------------------------------------------------------------ */
 /* Request server (continuous batching)                                */
 /* ------------------------------------------------------------------ */

@@ -16,6 +16,7 @@ from .fic import (  # noqa: F401
     fic_encode,
     fic_encode_batch,
     fic_encode_ex,
+    fic_pack,
     fic_stats_read,
     fic_stats_reset,
     fic_version,

@@ -22,8 +22,33 @@ namespace {
 struct Context {
     std::mutex mu;
     Engine eng;
-    DevBuf dec0, dec1, dcodes;
+    DevBuf dec0, dec1, dcodes, pack_sizes, pack_offs, pack_words;
 };
+
+// Most-significant-bit-first writer of the stored stream's header.
+struct BitWriter {
+    std::vector<uint8_t> buf;
+    int64_t bit = 0;
+    void put(uint64_t v, int nb)
+    {
+        for (int i = nb - 1; i >= 0; --i) {
+            if ((bit >> 3) >= (int64_t)buf.size()) buf.push_back(0);
+            if ((v >> i) & 1u) buf[(size_t)(bit >> 3)] |= (uint8_t)(0x80u >> (bit & 7));
+            ++bit;
+        }
+    }
+    void align()
+    {
+        while (bit & 7) put(0, 1);
+    }
+};
+
+int ceil_log2(int64_t v)
+{
+    int x = 0;
+    while (((int64_t)1 << x) < v) ++x;
+    return x;
+}
 
 std::mutex g_ctx_mu;
 Context* g_ctx[64] = {};
@@ -299,6 +324,145 @@ int fic_domain_pool(const uint8_t* img, int N, int B, int L, double entropy_thre
     FIC_TRY(cudaStreamSynchronize(s));
     if (pool_xy && cap < d) return FIC_ECAP;
     return FIC_OK;
+}
+
+int fic_pack(const uint8_t* img, const fic_params* p, const fic_result* r, uint8_t* out,
+             int64_t cap, int64_t* n_bytes, int64_t* payload_bits, void* stream)
+{
+    if (!img || !p || !r || !n_bytes || cap < 0 || (cap > 0 && !out)) return FIC_EINVAL;
+    fic_params prm = *p;
+    prm.N = r->N;
+    int nl = 0;
+    if (validate_params(&prm, prm.N, &nl) || nl != r->n_levels || prm.L > 65535) return FIC_EINVAL;
+    if (r->n_codes < 0 || (r->n_codes > 0 && !r->codes)) return FIC_EINVAL;
+    // record bits stay below 2^32 (at most 48 bits per record)
+    if (r->n_codes > ((int64_t)1 << 32) / 48) return FIC_EINVAL;
+    try {
+        cudaStream_t s = (cudaStream_t)stream;
+        Context* c = nullptr;
+        int st = get_context(&c, s);
+        if (st) return st;
+        std::lock_guard<std::mutex> guard(c->mu);
+        Engine& E = c->eng;
+        st = E.ensure_slots(1);
+        if (st) return st;
+        ImageWork& w = E.work(0);
+        const int N = prm.N;
+        const uint8_t* dimg = img;
+        if (!is_device_ptr(img)) {
+            FIC_TRY(w.img.ensure((size_t)N * N));
+            FIC_TRY(cudaMemcpyAsync(w.img.p, img, (size_t)N * N, cudaMemcpyHostToDevice, s));
+            dimg = w.img.as<uint8_t>();
+        }
+        Launcher Lk(s);
+        BitWriter bw;
+        for (const char ch : {'F', 'I', 'C', '1'}) bw.put((uint64_t)ch, 8);
+        bw.put((uint64_t)N, 16);
+        bw.put((uint64_t)prm.B_max, 8);
+        bw.put((uint64_t)nl, 8);
+        bw.put((uint64_t)prm.L, 16);
+        bw.put(prm.pool_dn > 0 ? 1u : 0u, 8);
+        bw.put((uint64_t)r->n_codes, 32);
+        PackLevels pl;
+        memset(&pl, 0, sizeof(pl));
+        const bool listed = prm.pool_dn > 0 || prm.entropy_thresh >= 0.0;
+        std::vector<uint32_t> list;
+        for (int l = 0; l < nl; ++l) {
+            const fic_sset& ss = prm.S_sets[l];
+            bw.put((uint64_t)ss.n_s, 8);
+            bw.put((uint64_t)ss.q, 16);
+            for (int i = 0; i < ss.n_s; ++i) bw.put((uint64_t)ss.p[i], 16);
+            const int B = prm.B_max >> l;
+            const int per = positions_per_axis(N, B, prm.L);
+            const int64_t npos = (int64_t)per * per;
+            int64_t dn = 0;
+            list.clear();
+            if (r->ranges[l] > 0) {
+                if (listed) {
+                    int64_t near = 0;
+                    st = E.pool_only(0, dimg, N, B, prm.L,
+                                     prm.pool_dn > 0 ? -1.0 : prm.entropy_thresh, prm.pool_dn,
+                                     false, Lk, s, &dn, &near);
+                    if (st) return st;
+                    list.resize((size_t)dn);
+                    if (dn > 0) {
+                        FIC_TRY(cudaMemcpyAsync(list.data(), w.pool.p, sizeof(uint32_t) * dn,
+                                                cudaMemcpyDeviceToHost, s));
+                        FIC_TRY(cudaStreamSynchronize(s));
+                    }
+                } else {
+                    dn = npos;
+                }
+            }
+            // the result must come from this image and these parameters
+            if (dn != (r->ranges[l] > 0 ? r->pool_size[l] : 0)) return FIC_EINVAL;
+            bw.put((uint64_t)dn, 32);
+            const int pw = ceil_log2(per);
+            int form = 0;
+            if (dn > 0 && dn < npos) form = (dn * 2 * pw <= npos) ? 1 : 2;
+            bw.put((uint64_t)form, 8);
+            if (form == 1) {
+                for (int64_t i = 0; i < dn; ++i) {
+                    bw.put((list[(size_t)i] & 0xffffu) / (uint32_t)prm.L, pw);
+                    bw.put((list[(size_t)i] >> 16) / (uint32_t)prm.L, pw);
+                }
+            } else if (form == 2) {
+                int64_t k = 0;
+                for (int64_t i = 0; i < npos; ++i) {
+                    const uint32_t xy = (uint32_t)((i % per) * prm.L) |
+                                        ((uint32_t)((i / per) * prm.L) << 16);
+                    const bool in = k < dn && list[(size_t)k] == xy;
+                    if (in) ++k;
+                    bw.put(in ? 1u : 0u, 1);
+                }
+            }
+            bw.align();
+            pl.has_pool[l] = dn > 0;
+            pl.addr_bits[l] = ceil_log2(dn);
+            pl.s_bits[l] = ceil_log2(ss.n_s);
+        }
+        // the records, on the GPU
+        const int64_t n = r->n_codes;
+        const void* dcodes = r->codes;
+        if (n > 0 && !is_device_ptr(r->codes)) {
+            FIC_TRY(c->dcodes.ensure(sizeof(fic_code) * n));
+            FIC_TRY(cudaMemcpyAsync(c->dcodes.p, r->codes, sizeof(fic_code) * n,
+                                    cudaMemcpyHostToDevice, s));
+            dcodes = c->dcodes.p;
+        }
+        const int64_t n_words = (n * 48 + 31) / 32 + 1;
+        FIC_TRY(c->pack_sizes.ensure(sizeof(uint32_t) * (n ? n : 1)));
+        FIC_TRY(c->pack_offs.ensure(sizeof(uint32_t) * (n ? n : 1)));
+        FIC_TRY(c->pack_words.ensure(sizeof(uint32_t) * n_words));
+        FIC_TRY(w.scan_tmp.ensure(sizeof(uint32_t) * scan_tmp_words(n ? n : 1)));
+        Scalars* ds = E.dev_scalars();
+        Lk.begin(FIC_K_MISC);
+        FIC_TRY(launch_pack_records(dcodes, n, pl, c->pack_sizes.as<uint32_t>(),
+                                    c->pack_offs.as<uint32_t>(), w.scan_tmp.as<uint32_t>(),
+                                    &ds->total, c->pack_words.as<uint32_t>(), n_words, s));
+        Lk.end(4, 0.0, (double)n * 24.0);
+        st = E.read_scalars(1, s);
+        if (st) return st;
+        const int64_t bits = E.host_scalars(0).total;
+        const int64_t head = (int64_t)bw.buf.size();
+        const int64_t total = head + (bits + 7) / 8;
+        *n_bytes = total;
+        if (payload_bits) *payload_bits = bits;
+        if (!out) return FIC_OK;
+        if (cap < total) return FIC_ECAP;
+        std::vector<uint32_t> words((size_t)((bits + 31) / 32));
+        if (!words.empty()) {
+            FIC_TRY(cudaMemcpyAsync(words.data(), c->pack_words.p, sizeof(uint32_t) * words.size(),
+                                    cudaMemcpyDeviceToHost, s));
+            FIC_TRY(cudaStreamSynchronize(s));
+        }
+        memcpy(out, bw.buf.data(), (size_t)head);
+        for (int64_t k = 0; k < (bits + 7) / 8; ++k)
+            out[head + k] = (uint8_t)(words[(size_t)(k >> 2)] >> (24 - 8 * (k & 3)));
+        return FIC_OK;
+    } catch (...) {
+        return FIC_ENOMEM;
+    }
 }
 
 int fic_stats_reset(int timing)

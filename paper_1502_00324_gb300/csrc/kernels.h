@@ -89,6 +89,20 @@ cudaError_t launch_order_gather(const void* codes, const uint32_t* cellmap,
                                 const uint32_t* cellflag, const uint32_t* rank, int64_t n_cells,
                                 void* out, cudaStream_t s);
 
+// Field widths of the stored records per quadtree step.
+struct PackLevels {
+    int has_pool[4];   // the step's pool is not empty
+    int addr_bits[4];  // ceil(log2 DN)
+    int s_bits[4];     // ceil(log2 |S|)
+};
+// Bit fields of n records (device fic_code array) into words (n_words,
+// zeroed here); *total_bits (device) receives the payload size.  sizes and
+// offs: n words each; scan_tmp: scan_tmp_words(n) words.
+cudaError_t launch_pack_records(const void* codes, int64_t n, const PackLevels& pl,
+                                uint32_t* sizes, uint32_t* offs, uint32_t* scan_tmp,
+                                uint32_t* total_bits, uint32_t* words, int64_t n_words,
+                                cudaStream_t s);
+
 // S sets by quadtree step for the decoder (S = p[level][s] / q[level]).
 struct DecodeS {
     int B_max;

@@ -932,6 +932,73 @@ decode_pass_kernel(const fic_code* __restrict__ codes, int64_t n_codes, DecodeS 
     if (__any_sync(0xffffffffu, diff) && lane == 0) atomicOr(changed, 1u);
 }
 
+// ---------------------------------------------------------------------------
+// Stored stream records (Sec. 3.3, Fig. 7, eq. 8): step (2 bits), mean
+// (7 bits), then when the step's pool is not empty isometry (3 bits),
+// address (ceil(log2 DN) bits) and S index (ceil(log2 |S|) bits), most
+// significant bit first.  Sizes first, then (after an exclusive scan of
+// the sizes) every record ORs its bits into 32-bit words in which stream
+// bit b is word b / 32, bit 31 - b % 32.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int pack_record(const fic_code& c, const PackLevels& pl, uint64_t* v)
+{
+    const int l = c.level;
+    uint64_t x = ((uint64_t)l << 7) | (uint64_t)(c.o_q & 0x7f);
+    int nb = 9;
+    if (pl.has_pool[l]) {
+        x = (x << 3) | (uint64_t)(c.iso & 7);
+        x = (x << pl.addr_bits[l]) | (uint64_t)c.pool_idx;
+        x = (x << pl.s_bits[l]) | (uint64_t)c.s_idx;
+        nb += 3 + pl.addr_bits[l] + pl.s_bits[l];
+    }
+    *v = x;
+    return nb;
+}
+
+__global__ void pack_sizes_kernel(const fic_code* __restrict__ codes, int64_t n, PackLevels pl,
+                                  uint32_t* __restrict__ sizes)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t v;
+    sizes[i] = (uint32_t)pack_record(codes[i], pl, &v);
+}
+
+__global__ void pack_write_kernel(const fic_code* __restrict__ codes, int64_t n, PackLevels pl,
+                                  const uint32_t* __restrict__ offs, uint32_t* __restrict__ words)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t v;
+    int nb = pack_record(codes[i], pl, &v);
+    uint32_t b = offs[i];
+    while (nb > 0) {
+        const int room = 32 - (int)(b & 31);
+        const int take = nb < room ? nb : room;
+        const uint32_t part = (uint32_t)((v >> (nb - take)) & ((1ull << take) - 1ull));
+        atomicOr(&words[b >> 5], part << (room - take));
+        nb -= take;
+        b += (uint32_t)take;
+    }
+}
+
+cudaError_t launch_pack_records(const void* codes, int64_t n, const PackLevels& pl,
+                                uint32_t* sizes, uint32_t* offs, uint32_t* scan_tmp,
+                                uint32_t* total_bits, uint32_t* words, int64_t n_words,
+                                cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(words, 0, sizeof(uint32_t) * (size_t)(n_words ? n_words : 1), s);
+    if (e != cudaSuccess) return e;
+    if (n == 0) return cudaMemsetAsync(total_bits, 0, sizeof(uint32_t), s);
+    const fic_code* c = static_cast<const fic_code*>(codes);
+    const unsigned g = (unsigned)((n + 255) / 256);
+    pack_sizes_kernel<<<g, 256, 0, s>>>(c, n, pl, sizes);
+    e = launch_scan(sizes, offs, n, scan_tmp, total_bits, s, nullptr);
+    if (e != cudaSuccess) return e;
+    pack_write_kernel<<<g, 256, 0, s>>>(c, n, pl, offs, words);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_decode_pass(const void* codes, int64_t n_codes, const DecodeS& ds,
                                const uint8_t* src, uint8_t* dst, int N, unsigned* changed,
                                cudaStream_t s)

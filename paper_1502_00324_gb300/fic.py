@@ -86,7 +86,7 @@ assert CODE_DTYPE.itemsize == C.sizeof(FicCode) == 16
 
 EXPORTS = ["fic_encode", "fic_encode_ex", "fic_encode_batch", "fic_decode", "fic_domain_pool", "fic_result_free",
            "fic_strerror", "fic_stats_reset", "fic_stats_read", "fic_version",
-           "fic_domain_pool_noalloc", "fic_last_error", "fic_server_create", "fic_server_submit",
+           "fic_domain_pool_noalloc", "fic_last_error", "fic_pack", "fic_server_create", "fic_server_submit",
            "fic_server_poll", "fic_server_stats_read", "fic_server_destroy"]
 
 
@@ -131,6 +131,8 @@ def lib():
     L.fic_domain_pool_noalloc.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_double, vp,
                                           C.c_int64, C.POINTER(C.c_int64), vp,
                                           C.POINTER(C.c_int64), vp]
+    L.fic_pack.argtypes = [vp, C.POINTER(FicParams), C.POINTER(FicResult), vp, C.c_int64,
+                           C.POINTER(C.c_int64), C.POINTER(C.c_int64), vp]
     L.fic_server_create.argtypes = [C.POINTER(FicParams), C.POINTER(FicServerConfig),
                                     C.POINTER(vp)]
     L.fic_server_submit.argtypes = [vp, vp, C.c_int, C.POINTER(C.c_int64)]
@@ -288,6 +290,22 @@ def fic_encode(img, N, B_max, B_min, L, entropy_thresh, ssets, err_tol, stream=N
                           C.byref(res), _stream(stream))
     _check(st, "fic_encode")
     return _adopt(res)
+
+
+def fic_pack(img, enc: Encoded, B_max, B_min, L, entropy_thresh, ssets, err_tol,
+             engine=ENGINE_TENSOR, pool_dn=0, stream=None):
+    """The stored stream of an encode (bytes) and its record bits alone; the
+    arguments after ``enc`` are the encode's parameters."""
+    p = make_params(enc.N, B_max, B_min, L, entropy_thresh, ssets, err_tol, engine, pool_dn)
+    ip, keep = _ptr(img)
+    nb = C.c_int64(0)
+    pb = C.c_int64(0)
+    _check(lib().fic_pack(ip, C.byref(p), C.byref(enc._res), None, 0, C.byref(nb), C.byref(pb),
+                          _stream(stream)), "fic_pack")
+    out = np.zeros(max(int(nb.value), 1), np.uint8)
+    _check(lib().fic_pack(ip, C.byref(p), C.byref(enc._res), out.ctypes.data, out.size,
+                          C.byref(nb), C.byref(pb), _stream(stream)), "fic_pack")
+    return out[: int(nb.value)].tobytes(), int(pb.value)
 
 
 def fic_decode(enc: Encoded, iters_max=64, out=None, stream=None):
