@@ -61,6 +61,23 @@ def config_dict(w, extra=None):
     return d
 
 
+def measured_traffic():
+    """Mean DRAM bytes per contraction launch of one encode from the committed
+    ncu capture, or None when the kernel sources changed since."""
+    import hashlib
+    try:
+        prof = json.load(open(os.path.join(ROOT, "profiles", "contract_traffic_precision512.json")))
+        h = hashlib.sha1()
+        for f in prof["sources"]:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        if h.hexdigest() != prof["sources_sha1"]:
+            return None
+        ls = prof["launches"]
+        return sum(x["dram_read_bytes"] + x["dram_write_bytes"] for x in ls) / len(ls)
+    except Exception:
+        return None
+
+
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during a region."""
@@ -341,9 +358,13 @@ def run_gpu(args):
         "kernel_ms_per_step": kern_ms,
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_tf,
                      "unit": "TFLOP/s", "frac": (achieved / peak_tf) if achieved else None,
-                     "traffic": None, "kernel": "contract_tc_kernel",
-                     "peak_note": "measured bf16 dense burst (MEASURED_PEAKS.json); fp16 dense "
-                                  "nominal equal"},
+                     "traffic": None if args.only_side else measured_traffic(),
+                     "traffic_unit": "bytes per contraction launch (mean of the 3 steps)",
+                     "kernel": "contraction (contract_tc_kernel at 16x16, "
+                               "contract_tc_iso_kernel at 8x8 and 4x4)",
+                     "algorithmic_flops_per_encode": tc["flops"] / max(args.steps, 1),
+                     "peak_note": "of measured: bf16 dense burst (MEASURED_PEAKS.json); fp16 "
+                                  "dense nominal equal"},
         "cpu_baseline": cpu,
         "e2e": {"value": (e2e_m / e2e_s / 1e9) if e2e_m else None, "unit": "Gmatch/s",
                 "h2d_bytes_per_step": int(N * N), "d2h_bytes_per_step": int(r_t.n_codes * 16)},
