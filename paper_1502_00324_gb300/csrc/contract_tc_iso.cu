@@ -246,6 +246,8 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
         // ------------------------------------------------------------ producer
         // the whole warp walks the schedule; one elected lane issues copies
         int64_t it = 0, cfi = 0, icount = 0;
+        int sidx = 0, cidx = 0;          // ring positions of it and cfi
+        uint32_t sphase = 0, cphase = 0; // and their parities
         bool ok = true;
         for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
             const Problem& Q = P.probs[find_problem(P.probs, P.n_probs, item)];
@@ -265,26 +267,30 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
             __syncwarp();
             ++icount;
             for (int ct = ct0; ct < ct1 && ok; ++ct) {
-                const int cb = (int)(it % ncf);
-                const uint32_t cph = (uint32_t)((it / ncf) & 1);
-                if (!(ok = mbar_wait_warp(cfe(cb), cph ^ 1, err, kWaitCycles))) break;
+                if (!(ok = mbar_wait_warp(cfe(cidx), cphase ^ 1, err, kWaitCycles))) break;
                 if (elect_one()) {
-                    mbar_expect_tx(cff(cb), cf_bytes);
-                    bulk_g2s(smem_u32(sCF + (size_t)cb * cf_bytes), Q.cf + (int64_t)ct * kN * sp.cw,
-                             cf_bytes, cff(cb));
+                    mbar_expect_tx(cff(cidx), cf_bytes);
+                    bulk_g2s(smem_u32(sCF + (size_t)cidx * cf_bytes), Q.cf + (int64_t)ct * kN * sp.cw,
+                             cf_bytes, cff(cidx));
                 }
                 __syncwarp();
                 ++cfi;
-                const int s = (int)(it % nstage);
-                const uint32_t sph = (uint32_t)((it / nstage) & 1);
-                if (!(ok = mbar_wait_warp(empty(s), sph ^ 1, err, kWaitCycles))) break;
+                if (++cidx == ncf) {
+                    cidx = 0;
+                    cphase ^= 1;
+                }
+                if (!(ok = mbar_wait_warp(empty(sidx), sphase ^ 1, err, kWaitCycles))) break;
                 if (elect_one()) {
-                    mbar_expect_tx(full(s), kBStageBytes);
-                    bulk_g2s(smem_u32(sB + (size_t)s * kBStageBytes), Q.D + (int64_t)ct * kN * K,
-                             kBStageBytes, full(s));
+                    mbar_expect_tx(full(sidx), kBStageBytes);
+                    bulk_g2s(smem_u32(sB + (size_t)sidx * kBStageBytes), Q.D + (int64_t)ct * kN * K,
+                             kBStageBytes, full(sidx));
                 }
                 __syncwarp();
                 ++it;
+                if (++sidx == nstage) {
+                    sidx = 0;
+                    sphase ^= 1;
+                }
             }
         }
         if (!ok && lane == 0) {
@@ -301,7 +307,9 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
         // warp-uniform schedule with precomputed descriptors; one elected lane
         // issues the MMAs and commits
         const uint64_t a_desc = smem_desc(smem_u32(sA), 128u, kSbo);
-        int64_t it = 0, pcount = 0, icount = 0;
+        int64_t icount = 0;
+        int sidx = 0, slot = 0;          // D' stage and TMEM slot positions
+        uint32_t sphase = 0, tphase = 0; // and their parities
         bool ok = true;
         for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
             const Problem& Q = P.probs[find_problem(P.probs, P.n_probs, item)];
@@ -311,16 +319,13 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
             if (!(ok = mbar_wait_warp(a_full, (uint32_t)(icount & 1), err, kWaitCycles))) break;
             tc_fence_after();
             for (int ct = ct0; ct < ct1 && ok; ++ct) {
-                const int s = (int)(it % nstage);
-                const uint32_t sph = (uint32_t)((it / nstage) & 1);
-                if (!(ok = mbar_wait_warp(full(s), sph, err, kWaitCycles))) break;
+                if (!(ok = mbar_wait_warp(full(sidx), sphase, err, kWaitCycles))) break;
                 tc_fence_after();
                 const uint64_t b_desc =
-                    smem_desc(smem_u32(sB + (size_t)s * kBStageBytes), 128u, kSbo);
-                for (int pass = 0; pass < kPasses && ok; ++pass) {
-                    const int slot = (int)(pcount % kSlots);
-                    const uint32_t ph = (uint32_t)((pcount / kSlots) & 1);
-                    if (!(ok = mbar_wait_warp(tempty(slot), ph ^ 1, err, kWaitCycles))) break;
+                    smem_desc(smem_u32(sB + (size_t)sidx * kBStageBytes), 128u, kSbo);
+#pragma unroll
+                for (int pass = 0; pass < kPasses; ++pass) {
+                    if (!(ok = mbar_wait_warp(tempty(slot), tphase ^ 1, err, kWaitCycles))) break;
                     tc_fence_after();
                     if (elect_one()) {
 #pragma unroll
@@ -335,12 +340,18 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
                         tc_commit(tfull(slot));
                     }
                     __syncwarp();
-                    ++pcount;
+                    if (++slot == kSlots) {
+                        slot = 0;
+                        tphase ^= 1;
+                    }
                 }
                 if (!ok) break;
-                if (elect_one()) tc_commit(empty(s));  // every pass read this stage
+                if (elect_one()) tc_commit(empty(sidx));  // every pass read this stage
                 __syncwarp();
-                ++it;
+                if (++sidx == nstage) {
+                    sidx = 0;
+                    sphase ^= 1;
+                }
             }
             if (!ok) break;
             if (elect_one()) tc_commit(a_empty);
@@ -357,7 +368,8 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
         const int quad = warp & 3;   // TMEM lanes (ranges) 32 quad .. +31
         const int hsel = e >> 2;     // column slice of a tile
         const float inv_n = 1.0f / (float)sp.n;
-        int64_t it = 0, pcount = 0;
+        int cidx = 0, slot = 0;          // constants ring and TMEM slot positions
+        uint32_t cphase = 0, tphase = 0; // and their parities
         bool ok = true;
         for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
             const Problem& Q = P.probs[find_problem(P.probs, P.n_probs, item)];
@@ -375,14 +387,11 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
             row_state_init(st);
             if (valid) row_state_seed(st, Q.gbest + range, inv_n, r.delta);
             for (int ct = ct0; ct < ct1; ++ct) {
-                const int cb = (int)(it % ncf);
-                const uint32_t cph = (uint32_t)((it / ncf) & 1);
-                if (!(ok = mbar_wait(cff(cb), cph, err, kWaitCycles))) break;
-                const float* cfs = reinterpret_cast<const float*>(sCF + (size_t)cb * cf_bytes);
-                for (int pass = 0; pass < kPasses && ok; ++pass) {
-                    const int slot = (int)(pcount % kSlots);
-                    const uint32_t ph = (uint32_t)((pcount / kSlots) & 1);
-                    if (!(ok = mbar_wait(tfull(slot), ph, err, kWaitCycles))) break;
+                if (!(ok = mbar_wait(cff(cidx), cphase, err, kWaitCycles))) break;
+                const float* cfs = reinterpret_cast<const float*>(sCF + (size_t)cidx * cf_bytes);
+#pragma unroll 1
+                for (int pass = 0; pass < kPasses; ++pass) {
+                    if (!(ok = mbar_wait(tfull(slot), tphase, err, kWaitCycles))) break;
                     tc_fence_after();
                     const uint32_t tb = tmem_base + ((uint32_t)(quad * 32) << 16) +
                                         (uint32_t)(slot * kSlotCols + hsel * kWarpCols);
@@ -405,12 +414,18 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
                                                      -r.a, r.delta, inv_n, r.sr, qci, qdn, &sp);
                         }
                     }
-                    ++pcount;
+                    if (++slot == kSlots) {
+                        slot = 0;
+                        tphase ^= 1;
+                    }
                 }
                 if (!ok) break;
                 __syncwarp();
-                if (lane == 0) mbar_arrive(cfe(cb));
-                ++it;
+                if (lane == 0) mbar_arrive(cfe(cidx));
+                if (++cidx == ncf) {
+                    cidx = 0;
+                    cphase ^= 1;
+                }
             }
             if (!ok) break;
             if (valid) {
