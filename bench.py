@@ -562,9 +562,11 @@ COMPARE_DESC = ("compare: the 512x512 precision image (1/f texture, alpha 2, see
 
 
 def run_compare(args):
-    """Encode time and quality of the proposed method (predefined S per step)
-    against the entropy-based baseline (ten S values per step) on the same
-    top-DN pools (Sec. 4, Tables 2-3, eq. 9)."""
+    """Encode time, quality and stored size of the proposed method
+    (predefined S per step) against the entropy-based baseline (ten S values
+    per step) on the same top-DN pools (Sec. 4, Tables 2-3, eq. 9); the
+    stream is Sec. 3.3 / Fig. 7 / eq. 8 with the domain lists in its
+    header."""
     import torch
     import paper_1502_00324_gb300 as pkg
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -596,7 +598,13 @@ def run_compare(args):
                 ms.append(e0.elapsed_time(e1))
             rec, _ = pkg.fic_decode(r, iters_max=64)
             mse = float(np.mean((rec.astype(np.float64) - img) ** 2))
+            packed, rec_bits = pkg.fic_pack(dimg, r, 16, 2, 2, -1.0, ss, 8.0, pool_dn=dn,
+                                            stream=stream)
             row[name] = {"ms": statistics.median(ms), "records": r.n_codes,
+                         "stream_bytes": len(packed), "record_bits": rec_bits,
+                         "compression_ratio": 512 * 512 / len(packed),
+                         "compression_ratio_records_only": 512 * 512 * 8 / rec_bits,
+                         "bpp": 8.0 * len(packed) / (512 * 512),
                          "records_per_step": [int((r.codes["level"] == l).sum())
                                               for l in range(4)],
                          "psnr_db": 10 * np.log10(255.0 ** 2 / mse) if mse > 0 else None,

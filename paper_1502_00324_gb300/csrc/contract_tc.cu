@@ -135,7 +135,9 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
     if (warp == 0) {
         // ------------------------------------------------------------ producer
         // the whole warp walks the schedule; one elected lane issues copies
-        int64_t it = 0, tcount = 0, cfi = 0, icount = 0;
+        int64_t it = 0, cfi = 0, icount = 0;
+        int sidx = 0, cidx = 0;          // ring positions of it and cfi
+        uint32_t sphase = 0, cphase = 0; // and their parities
         bool ok = true;
         for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
             const Problem& Q = P.probs[find_problem(P.probs, P.n_probs, item)];
@@ -154,30 +156,33 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
             __syncwarp();
             ++icount;
             for (int ct = ct0; ct < ct1 && ok; ++ct) {
-                const int cb = (int)(tcount % ncf);
-                const uint32_t cph = (uint32_t)((tcount / ncf) & 1);
-                if (!(ok = mbar_wait_warp(cfe(cb), cph ^ 1, err, kWaitCycles))) break;
+                if (!(ok = mbar_wait_warp(cfe(cidx), cphase ^ 1, err, kWaitCycles))) break;
                 if (elect_one()) {
-                    mbar_expect_tx(cff(cb), cf_bytes);
-                    bulk_g2s(smem_u32(sCF + (size_t)cb * cf_bytes), Q.cf + (int64_t)ct * kN * sp.cw,
-                             cf_bytes, cff(cb));
+                    mbar_expect_tx(cff(cidx), cf_bytes);
+                    bulk_g2s(smem_u32(sCF + (size_t)cidx * cf_bytes), Q.cf + (int64_t)ct * kN * sp.cw,
+                             cf_bytes, cff(cidx));
                 }
                 __syncwarp();
                 ++cfi;
+                if (++cidx == ncf) {
+                    cidx = 0;
+                    cphase ^= 1;
+                }
                 for (int kb = 0; kb < NKB; ++kb) {
-                    const int s = (int)(it % nstage);
-                    const uint32_t sph = (uint32_t)((it / nstage) & 1);
-                    if (!(ok = mbar_wait_warp(empty(s), sph ^ 1, err, kWaitCycles))) break;
+                    if (!(ok = mbar_wait_warp(empty(sidx), sphase ^ 1, err, kWaitCycles))) break;
                     if (elect_one()) {
-                        mbar_expect_tx(full(s), kBStageBytes);
-                        bulk_g2s(smem_u32(sB + (size_t)s * kBStageBytes),
+                        mbar_expect_tx(full(sidx), kBStageBytes);
+                        bulk_g2s(smem_u32(sB + (size_t)sidx * kBStageBytes),
                                  Q.D + ((int64_t)kb * Q.cols_pad * KB + (int64_t)ct * kN * KB),
-                                 kBStageBytes, full(s));
+                                 kBStageBytes, full(sidx));
                     }
                     __syncwarp();
                     ++it;
+                    if (++sidx == nstage) {
+                        sidx = 0;
+                        sphase ^= 1;
+                    }
                 }
-                ++tcount;
             }
         }
         if (!ok && lane == 0) {
@@ -192,7 +197,9 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         const uint64_t a_desc = smem_desc(smem_u32(sA), 128u, kSbo);
-        int64_t it = 0, tcount = 0, icount = 0;
+        int64_t tcount = 0, icount = 0;
+        int sidx = 0;                    // D' stage ring position
+        uint32_t sphase = 0;             // and its parity
         bool ok = true;
         for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
             const Problem& Q = P.probs[find_problem(P.probs, P.n_probs, item)];
@@ -208,21 +215,23 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + (uint32_t)acc * 256u;  // 256-column slots
                 for (int kb = 0; kb < NKB; ++kb) {
-                    const int s = (int)(it % nstage);
-                    const uint32_t sph = (uint32_t)((it / nstage) & 1);
-                    if (!(ok = mbar_wait_warp(full(s), sph, err, kWaitCycles))) break;
+                    if (!(ok = mbar_wait_warp(full(sidx), sphase, err, kWaitCycles))) break;
                     tc_fence_after();
                     const uint64_t ak = desc_add(a_desc, (uint32_t)kb * kAKBBytes);
-                    const uint64_t bk = smem_desc(smem_u32(sB + (size_t)s * kBStageBytes), 128u, kSbo);
+                    const uint64_t bk =
+                        smem_desc(smem_u32(sB + (size_t)sidx * kBStageBytes), 128u, kSbo);
                     if (elect_one()) {
 #pragma unroll
                         for (int j = 0; j < KB / 16; ++j)
                             tc_mma_f16(d_tmem, desc_add(ak, 256u * j), desc_add(bk, 256u * j), kIdesc,
                                        (kb | j) != 0 ? 1u : 0u);
-                        tc_commit(empty(s));
+                        tc_commit(empty(sidx));
                     }
                     __syncwarp();
-                    ++it;
+                    if (++sidx == nstage) {
+                        sidx = 0;
+                        sphase ^= 1;
+                    }
                 }
                 if (!ok) break;
                 if (elect_one()) tc_commit(tfull(acc));
@@ -245,6 +254,8 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
         const int cq = e >> 2;              // column slice cq of a tile
         const float inv_n = 1.0f / (float)sp.n;
         int64_t tcount = 0;
+        int cidx = 0;                    // constants ring position
+        uint32_t cphase = 0;             // and its parity
         bool ok = true;
         for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
             const Problem& Q = P.probs[find_problem(P.probs, P.n_probs, item)];
@@ -266,10 +277,9 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
             for (int ct = ct0; ct < ct1; ++ct) {
                 const int acc = (int)(tcount & 1);
                 const uint32_t ph = (uint32_t)((tcount >> 1) & 1);
-                const int cb = (int)(tcount % ncf);
-                const uint32_t cph = (uint32_t)((tcount / ncf) & 1);
+                const int cb = cidx;
                 if (!(ok = mbar_wait(tfull(acc), ph, err, kWaitCycles))) break;
-                if (!(ok = mbar_wait(cff(cb), cph, err, kWaitCycles))) break;
+                if (!(ok = mbar_wait(cff(cb), cphase, err, kWaitCycles))) break;
                 tc_fence_after();
                 const float* cfs = reinterpret_cast<const float*>(sCF + (size_t)cb * cf_bytes);
                 const uint32_t tb = tmem_base + ((uint32_t)(quad * 32) << 16) +
@@ -329,6 +339,10 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
                 __syncwarp();
                 if (lane == 0) mbar_arrive(cfe(cb));
                 ++tcount;
+                if (++cidx == ncf) {
+                    cidx = 0;
+                    cphase ^= 1;
+                }
             }
             if (!ok) break;
             if (valid) row_state_publish(st, Q.gbest + row);
