@@ -324,6 +324,38 @@ void fic_result_free(fic_result* r);
 const char* fic_strerror(int status);
 
 /* ------------------------------------------------------------------ */
+/* Contraction shape tuning                                            */
+/* ------------------------------------------------------------------ */
+/* The contraction of a quadtree step can run with several tile shapes that
+ * give identical records: isometry-in-accumulator tiles (128 ranges x 64
+ * pool domains x 8 isometries; 2x2 to 8x8 ranges with at most 3 S values)
+ * or row tiles (128 (range, isometry) rows x 256 domains), each with a work
+ * chunking tuned for a per-item refill cost of 1, 2 or 4 tiles.  In mode 1
+ * (the default) the first step of each (engine, K = B*B padded, |S|, size
+ * class = floor(log2(ranges x pool domains))) runs every candidate once on
+ * its own operands, timed with CUDA events, and keeps the fastest for that
+ * class (per engine: the synchronous entry points share one per device;
+ * each server has its own).  Mode 0: the fixed default (isometry tiles
+ * where they apply, refill 2); mode 2 + i: candidate i for every step
+ * (i taken modulo the step's candidate count).  The paper has no
+ * counterpart; this is the GPU design's tile-shape choice. */
+typedef struct {
+    int32_t engine, K, n_s, size_class;  /* the class                      */
+    int32_t iso_tiles;                   /* 1: isometry tiles; 0: row tiles */
+    int32_t refill;                      /* chunking refill cost, tiles     */
+    float ms;                            /* measured contraction time       */
+    int32_t candidates;                  /* shapes measured                 */
+} fic_tune_entry;
+
+/* fic_tune_mode -- set the mode (mode >= 0) and/or read the previous one
+ * (previous may be NULL; mode < 0 only reads).  Process-wide. */
+int fic_tune_mode(int mode, int* previous);
+/* fic_tune_read -- the tuned classes of the synchronous entry points'
+ * engine on the current device: up to cap entries into out (host), *n the
+ * total. */
+int fic_tune_read(fic_tune_entry* out, int cap, int* n);
+
+/* ------------------------------------------------------------------ */
 /* Instrumentation                                                     */
 /* ------------------------------------------------------------------ */
 #define FIC_K_ENTROPY 0

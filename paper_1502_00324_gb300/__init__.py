@@ -17,6 +17,8 @@ from .fic import (  # noqa: F401
     fic_encode_batch,
     fic_encode_ex,
     fic_pack,
+    fic_tune_mode,
+    fic_tune_read,
     fic_stats_read,
     fic_stats_reset,
     fic_version,

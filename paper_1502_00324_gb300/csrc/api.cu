@@ -465,6 +465,35 @@ int fic_pack(const uint8_t* img, const fic_params* p, const fic_result* r, uint8
     }
 }
 
+int fic_tune_mode(int mode, int* previous)
+{
+    if (previous) *previous = tune_mode();
+    if (mode >= 0) set_tune_mode(mode);
+    return FIC_OK;
+}
+
+int fic_tune_read(fic_tune_entry* out, int cap, int* n)
+{
+    if (!n || cap < 0 || (cap > 0 && !out)) return FIC_EINVAL;
+    Context* c = nullptr;
+    int st = get_context(&c, nullptr);
+    if (st) return st;
+    std::lock_guard<std::mutex> guard(c->mu);
+    const auto& t = c->eng.tuned();
+    *n = (int)t.size();
+    for (int i = 0; i < cap && i < (int)t.size(); ++i) {
+        out[i].engine = t[(size_t)i].engine;
+        out[i].K = t[(size_t)i].K;
+        out[i].n_s = t[(size_t)i].ns;
+        out[i].size_class = t[(size_t)i].size_class;
+        out[i].iso_tiles = t[(size_t)i].choice.iso;
+        out[i].refill = t[(size_t)i].choice.refill;
+        out[i].ms = t[(size_t)i].ms;
+        out[i].candidates = t[(size_t)i].candidates;
+    }
+    return FIC_OK;
+}
+
 int fic_stats_reset(int timing)
 {
     std::lock_guard<std::mutex> g(g_stats.mu);

@@ -8,6 +8,7 @@
 //              over the work items of all jobs at that step
 //           -> per job split decision -> scan -> records / children
 //   finish: record ordering (raster of top ranges, then TL, TR, BL, BR).
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -149,32 +150,48 @@ StepParams make_step(const fic_sset& s, int n)
     return sp;
 }
 
-// Engine-dependent shape of one quadtree step.
+// Engine-dependent shape of one quadtree step under a tuning choice.
 struct StepShape {
     int B, n2, K;
     StepParams sp;
     bool iso;            // isometry-in-accumulator tensor kernel
     int64_t tile_w;      // pool columns per tile
     int parts_per_chunk; // partial bests per (range, column chunk)
+    int refill;          // chunking: per-item refill cost in tiles
 };
 
-StepShape step_shape(const fic_params& p, int lvl)
+StepShape step_shape(const fic_params& p, int lvl, const TuneChoice& v)
 {
     StepShape h;
     h.B = p.B_max >> lvl;
     h.n2 = h.B * h.B;
     h.K = k_pad(h.n2);
     h.sp = make_step(p.S_sets[lvl], h.n2);
-    // 2x2 .. 8x8 ranges with up to 3 S values: ranges in TMEM lanes, one
-    // accumulator per isometry (iso-major A); otherwise rows are (range,
-    // isometry) pairs
+    // isometry-in-accumulator kernel: ranges in TMEM lanes, one accumulator
+    // per isometry (iso-major A); row kernel: rows are (range, isometry)
     const bool tc = p.engine == FIC_ENGINE_TENSOR;
-    h.iso = tc && contract_tc_iso_supports(h.K, h.sp.ns);
+    h.iso = tc && v.iso && contract_tc_iso_supports(h.K, h.sp.ns);
     h.tile_w = h.iso ? contract_tc_iso_ntile(h.K) : (tc ? contract_tc_ntile() : kPlainNTile);
     h.parts_per_chunk =
         h.iso ? contract_tc_iso_parts_per_chunk() : (tc ? contract_tc_parts_per_chunk() : 1);
+    h.refill = v.refill > 0 ? v.refill : 2;
     return h;
 }
+
+// The shapes the tuner tries for a step (all give identical records).
+std::vector<TuneChoice> tune_candidates(const fic_params& p, int lvl)
+{
+    const int B = p.B_max >> lvl;
+    const int K = k_pad(B * B);
+    const bool iso_ok =
+        p.engine == FIC_ENGINE_TENSOR && contract_tc_iso_supports(K, p.S_sets[lvl].n_s);
+    std::vector<TuneChoice> c;
+    for (int refill : {1, 2, 4}) c.push_back(TuneChoice{iso_ok ? 1 : 0, refill});
+    if (iso_ok) c.push_back(TuneChoice{0, 2});  // the row kernel on the same step
+    return c;
+}
+
+TuneChoice default_choice() { return TuneChoice{1, 2}; }
 
 int64_t rows_pad_for(const StepShape& h, int64_t R)
 {
@@ -199,12 +216,12 @@ int64_t max_chunks(int sm_count, int64_t n_mtiles, int64_t n_ct)
 
 // A problem alone in its launch: the chunk count that minimises the
 // estimated makespan over one item per SM (waves x tiles per item, plus a
-// per-item cost of refilling the pipeline).
-void choose_chunks_alone(int sm_count, int64_t n_mtiles, int64_t n_ct, int* n_chunks,
-                         int* per_chunk)
+// per-item cost of refilling the pipeline, refill tiles).
+void choose_chunks_alone(int sm_count, int64_t n_mtiles, int64_t n_ct, int refill,
+                         int* n_chunks, int* per_chunk)
 {
     const int64_t slots = sm_count;
-    const double item_cost = 2.0;  // in tiles
+    const double item_cost = (double)refill;  // in tiles
     int64_t best_nc = 1;
     double best = 1e300;
     const int64_t max_nc = max_chunks(sm_count, n_mtiles, n_ct);
@@ -224,7 +241,8 @@ void choose_chunks_alone(int sm_count, int64_t n_mtiles, int64_t n_ct, int* n_ch
 }
 
 // Several problems in one launch: items of about tiles_per_item column
-// tiles (total tiles / (8 x SMs)), so the persistent CTAs stay balanced.
+// tiles (total tiles / (16 / refill x SMs)), so the persistent CTAs stay
+// balanced.
 void choose_chunks_shared(int sm_count, int64_t n_mtiles, int64_t n_ct, double tiles_per_item,
                           int* n_chunks, int* per_chunk)
 {
@@ -243,6 +261,10 @@ void choose_chunks_shared(int sm_count, int64_t n_mtiles, int64_t n_ct, double t
 }  // namespace
 
 int positions_per_axis(int N, int B, int L) { return (N >= 2 * B) ? (N - 2 * B) / L + 1 : 0; }
+
+static std::atomic<int> g_tune_mode{1};
+int tune_mode() { return g_tune_mode.load(); }
+void set_tune_mode(int mode) { g_tune_mode.store(mode); }
 
 int validate_params(const fic_params* p, int N, int* n_levels)
 {
@@ -326,7 +348,7 @@ int64_t Engine::slot_bytes(int N, const fic_params& p) const
                     + cells * (2 * 16 + 2 * 4 + 3 * 4);   // records x2, act x2, order maps
     int64_t peak = 0;
     for (int lvl = 0; lvl < nl; ++lvl) {
-        const StepShape h = step_shape(p, lvl);
+        const StepShape h = step_shape(p, lvl, default_choice());
         const int per = positions_per_axis(N, h.B, p.L);
         const int64_t npos = (int64_t)per * per;
         const int64_t R = (int64_t)(N / h.B) * (N / h.B);
@@ -495,22 +517,64 @@ int Engine::step(const fic_params& p, const std::vector<Job*>& jobs, Launcher& L
         }
     }
 
+    // the contraction shape of each quadtree step present: tuned, fixed or
+    // forced (a step not seen before in tuning mode is measured below)
+    TuneChoice choice[FIC_MAX_LEVELS];
+    bool trial[FIC_MAX_LEVELS] = {false, false, false, false};
+    int tkey[FIC_MAX_LEVELS][4];
+    {
+        double work[FIC_MAX_LEVELS] = {0, 0, 0, 0};
+        for (Job* j : live) work[j->lvl] += (double)j->R * (double)j->dn;
+        const int mode = tune_mode();
+        for (int lvl = 0; lvl < nl; ++lvl) {
+            choice[lvl] = default_choice();
+            const int B = p.B_max >> lvl;
+            tkey[lvl][0] = p.engine;
+            tkey[lvl][1] = k_pad(B * B);
+            tkey[lvl][2] = p.S_sets[lvl].n_s;
+            tkey[lvl][3] = (int)std::floor(std::log2(work[lvl] + 1.0));
+            if (work[lvl] <= 0.0) continue;
+            const std::vector<TuneChoice> cand = tune_candidates(p, lvl);
+            if (mode >= 2) {
+                choice[lvl] = cand[(size_t)(mode - 2) % cand.size()];
+            } else if (mode == 1 && cand.size() > 1) {
+                trial[lvl] = true;
+                for (const TuneEntry& t : tuned_)
+                    if (t.engine == tkey[lvl][0] && t.K == tkey[lvl][1] && t.ns == tkey[lvl][2] &&
+                        t.size_class == tkey[lvl][3]) {
+                        choice[lvl] = t.choice;
+                        trial[lvl] = false;
+                    }
+            }
+        }
+    }
+
+    // operand A' and the range constants in the layout of a shape
+    auto prep = [&](Job* j, const StepShape& h) -> int {
+        ImageWork* w = work_[(size_t)j->slot].get();
+        j->rows_pad = rows_pad_for(h, j->R);
+        const int64_t rows_max = 8 * round_up(j->R, 128);  // either layout
+        FIC_TRY(w->A.ensure(sizeof(__half) * rows_max * h.K));
+        FIC_TRY(w->rc.ensure(sizeof(RowConst) * (rows_max / 8)));
+        L.begin(FIC_K_RANGE_PREP);
+        FIC_TRY(launch_range_prep(j->dimg, j->N, h.B, j->act, (int)j->R, j->rows_pad, h.K, h.sp,
+                                  &ds[j->slot].vd_max, h.iso ? 1 : 0, w->A.as<__half>(),
+                                  w->rc.as<RowConst>(), s));
+        L.end(1, 0.0, (double)j->rows_pad * h.K * 2.0 + (double)j->R * (h.n2 + 20.0));
+        return FIC_OK;
+    };
+
     // domain gathers and range preps
-    double group_tiles[FIC_MAX_LEVELS] = {0, 0, 0, 0};
-    int group_jobs[FIC_MAX_LEVELS] = {0, 0, 0, 0};
     for (Job* j : live) {
-        const StepShape h = step_shape(p, j->lvl);
+        const StepShape h = step_shape(p, j->lvl, choice[j->lvl]);
         ImageWork* w = work_[(size_t)j->slot].get();
         Scalars* d = ds + j->slot;
         j->res.pool_size[j->lvl] = j->dn;
         j->res.matches[j->lvl] = 8 * j->R * j->dn;
         j->cols_pad = round_up(j->dn > 0 ? j->dn : 1, kColPad);
-        j->rows_pad = rows_pad_for(h, j->R);
         FIC_TRY(w->D.ensure(sizeof(__half) * j->cols_pad * h.K));
         FIC_TRY(w->cf.ensure(sizeof(float) * j->cols_pad * h.sp.cw));
         FIC_TRY(w->ci.ensure(sizeof(ColExact) * j->cols_pad));
-        FIC_TRY(w->A.ensure(sizeof(__half) * j->rows_pad * h.K));
-        FIC_TRY(w->rc.ensure(sizeof(RowConst) * (j->rows_pad / 8)));
         FIC_TRY(w->best.ensure(sizeof(Best) * j->R));
         FIC_TRY(w->split.ensure(sizeof(uint32_t) * j->R));
         FIC_TRY(w->split_pos.ensure(sizeof(uint32_t) * j->R));
@@ -525,25 +589,23 @@ int Engine::step(const fic_params& p, const std::vector<Job*>& jobs, Launcher& L
         L.end(2, 0.0,
               (double)j->cols_pad * (2.0 * h.K + 4.0 * h.sp.cw + 8.0) +
                   (double)j->dn * 2.0 * h.n2);
-        L.begin(FIC_K_RANGE_PREP);
-        FIC_TRY(launch_range_prep(j->dimg, j->N, h.B, j->act, (int)j->R, j->rows_pad, h.K, h.sp,
-                                  &d->vd_max, h.iso ? 1 : 0, w->A.as<__half>(),
-                                  w->rc.as<RowConst>(), s));
-        L.end(1, 0.0, (double)j->rows_pad * h.K * 2.0 + (double)j->R * (h.n2 + 20.0));
-        if (j->dn > 0) {
-            group_tiles[j->lvl] +=
-                (double)mtiles_for(h, j->rows_pad) * (double)(j->cols_pad / h.tile_w);
-            group_jobs[j->lvl] += 1;
-        }
+        st = prep(j, h);
+        if (st) return st;
         j->n_chunks = 0;
         j->n_parts = 0;
     }
 
-    // one contraction launch per quadtree step present
+    // one contraction launch per quadtree step present (over every job at
+    // that step); timed with events when the tuner measures a shape
     int leaders[FIC_MAX_LEVELS] = {-1, -1, -1, -1};
-    for (int lvl = 0; lvl < nl; ++lvl) {
-        if (group_jobs[lvl] == 0) continue;
-        const StepShape h = step_shape(p, lvl);
+    auto run_group = [&](int lvl, const StepShape& h, float* ms) -> int {
+        double group_tiles = 0.0;
+        int group_jobs = 0;
+        for (Job* j : live)
+            if (j->lvl == lvl && j->dn > 0) {
+                group_tiles += (double)mtiles_for(h, j->rows_pad) * (double)(j->cols_pad / h.tile_w);
+                ++group_jobs;
+            }
         table_.clear();
         int64_t items = 0;
         double flops = 0.0, bytes = 0.0;
@@ -553,11 +615,12 @@ int Engine::step(const fic_params& p, const std::vector<Job*>& jobs, Launcher& L
             ImageWork* w = work_[(size_t)j->slot].get();
             const int64_t n_mtiles = mtiles_for(h, j->rows_pad);
             const int64_t n_ct = j->cols_pad / h.tile_w;
-            if (group_jobs[lvl] == 1)
-                choose_chunks_alone(sm_count_, n_mtiles, n_ct, &j->n_chunks, &j->per_chunk);
+            if (group_jobs == 1)
+                choose_chunks_alone(sm_count_, n_mtiles, n_ct, h.refill, &j->n_chunks,
+                                    &j->per_chunk);
             else
                 choose_chunks_shared(sm_count_, n_mtiles, n_ct,
-                                     group_tiles[lvl] / (8.0 * sm_count_), &j->n_chunks,
+                                     group_tiles / ((16.0 / h.refill) * sm_count_), &j->n_chunks,
                                      &j->per_chunk);
             j->n_parts = h.parts_per_chunk * j->n_chunks;
             FIC_TRY(w->part.ensure(sizeof(Best) * j->R * j->n_parts));
@@ -600,6 +663,12 @@ int Engine::step(const fic_params& p, const std::vector<Job*>& jobs, Launcher& L
         a.sp = h.sp;
         a.err = &ds[leaders[lvl]].err;
         a.grid_ctas = sm_count_;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (ms) {
+            FIC_TRY(cudaEventCreate(&e0));
+            FIC_TRY(cudaEventCreate(&e1));
+            FIC_TRY(cudaEventRecord(e0, s));
+        }
         if (p.engine == FIC_ENGINE_TENSOR) {
             FIC_TRY(cudaMemsetAsync(a.err, 0, 2 * sizeof(int), s));
             L.begin(FIC_K_CONTRACT_TC);
@@ -610,11 +679,76 @@ int Engine::step(const fic_params& p, const std::vector<Job*>& jobs, Launcher& L
             FIC_TRY(launch_contract_plain(a, s));
             L.end(1, flops, bytes, matches);
         }
+        if (ms) {
+            FIC_TRY(cudaEventRecord(e1, s));
+            FIC_TRY(cudaEventSynchronize(e1));
+            FIC_TRY(cudaEventElapsedTime(ms, e0, e1));
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            // a tuning run that gave up waiting must not be mistaken for a fast one
+            Scalars chk;
+            FIC_TRY(cudaMemcpy(&chk, &ds[leaders[lvl]], sizeof(chk), cudaMemcpyDeviceToHost));
+            if (p.engine == FIC_ENGINE_TENSOR && (chk.err || chk.err2)) return FIC_ETIMEOUT;
+        }
+        return FIC_OK;
+    };
+
+    for (int lvl = 0; lvl < nl; ++lvl) {
+        bool present = false;
+        for (Job* j : live) present |= (j->lvl == lvl && j->dn > 0);
+        if (!present) continue;
+        if (trial[lvl]) {
+            // measure every candidate on this step's operands, keep the fastest
+            const std::vector<TuneChoice> cand = tune_candidates(p, lvl);
+            float best_ms = 3.4e38f;
+            TuneChoice best = choice[lvl];
+            bool layout_iso = step_shape(p, lvl, choice[lvl]).iso;
+            for (const TuneChoice& c : cand) {
+                const StepShape h = step_shape(p, lvl, c);
+                if (h.iso != layout_iso) {
+                    for (Job* j : live)
+                        if (j->lvl == lvl) {
+                            st = prep(j, h);
+                            if (st) return st;
+                        }
+                    layout_iso = h.iso;
+                }
+                float ms = 0.0f;
+                st = run_group(lvl, h, &ms);
+                if (st) return st;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = c;
+                }
+            }
+            TuneEntry t;
+            t.engine = tkey[lvl][0];
+            t.K = tkey[lvl][1];
+            t.ns = tkey[lvl][2];
+            t.size_class = tkey[lvl][3];
+            t.choice = best;
+            t.ms = best_ms;
+            t.candidates = (int)cand.size();
+            tuned_.push_back(t);
+            choice[lvl] = best;
+            const StepShape h = step_shape(p, lvl, best);
+            if (h.iso != layout_iso)
+                for (Job* j : live)
+                    if (j->lvl == lvl) {
+                        st = prep(j, h);
+                        if (st) return st;
+                    }
+            st = run_group(lvl, h, nullptr);
+            if (st) return st;
+        } else {
+            st = run_group(lvl, step_shape(p, lvl, choice[lvl]), nullptr);
+            if (st) return st;
+        }
     }
 
     // split / requeue
     for (Job* j : live) {
-        const StepShape h = step_shape(p, j->lvl);
+        const StepShape h = step_shape(p, j->lvl, choice[j->lvl]);
         ImageWork* w = work_[(size_t)j->slot].get();
         const uint32_t* pool_xy = j->use_list ? w->pool.as<uint32_t>() : nullptr;
         const int last = (j->lvl == nl - 1);

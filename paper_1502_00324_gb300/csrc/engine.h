@@ -114,6 +114,19 @@ struct Job {
     fic_result res{};               // counters; codes set by finish()
 };
 
+// A contraction shape choice of the tuner: kernel family (1: isometry-in-
+// accumulator tiles where they apply, 0: row tiles) and the chunking's
+// per-item refill cost in tiles.
+struct TuneChoice {
+    int iso;
+    int refill;
+};
+
+// Tuning mode (process-wide): 0 fixed default shape, 1 measure on first use
+// (default), 2 + i force candidate i (tests).
+int tune_mode();
+void set_tune_mode(int mode);
+
 int validate_params(const fic_params* p, int N, int* n_levels);
 int positions_per_axis(int N, int B, int L);
 
@@ -155,6 +168,14 @@ public:
     Scalars* dev_scalars() { return scal_.as<Scalars>(); }
     const Scalars& host_scalars(int slot) const { return host_scal_[slot]; }
     int read_scalars(int n, cudaStream_t s);
+    // The tuned shapes so far: (engine, K, |S|, size class) -> choice, ms.
+    struct TuneEntry {
+        int engine, K, ns, size_class;
+        TuneChoice choice;
+        float ms;
+        int candidates;
+    };
+    const std::vector<TuneEntry>& tuned() const { return tuned_; }
 
 private:
     int launch_pool(Job& j, int B, int L_step, double thr, int64_t top, bool want_H,
@@ -166,6 +187,7 @@ private:
     int scal_cap_ = 0;
     std::vector<std::unique_ptr<ImageWork>> work_;
     std::vector<Problem> table_;
+    std::vector<TuneEntry> tuned_;
 };
 
 bool is_device_ptr(const void* p);

@@ -74,6 +74,12 @@ class FicServerStats(C.Structure):
                 ("hbm_budget", C.c_int64), ("matches", C.c_int64), ("busy_ms", C.c_double)]
 
 
+class FicTuneEntry(C.Structure):
+    _fields_ = [("engine", C.c_int32), ("K", C.c_int32), ("n_s", C.c_int32),
+                ("size_class", C.c_int32), ("iso_tiles", C.c_int32), ("refill", C.c_int32),
+                ("ms", C.c_float), ("candidates", C.c_int32)]
+
+
 class FicStats(C.Structure):
     _fields_ = [("launches", C.c_int64 * 10), ("ms", C.c_double * 10),
                 ("flops", C.c_double * 10), ("bytes", C.c_double * 10), ("matches", C.c_int64)]
@@ -86,7 +92,8 @@ assert CODE_DTYPE.itemsize == C.sizeof(FicCode) == 16
 
 EXPORTS = ["fic_encode", "fic_encode_ex", "fic_encode_batch", "fic_decode", "fic_domain_pool", "fic_result_free",
            "fic_strerror", "fic_stats_reset", "fic_stats_read", "fic_version",
-           "fic_domain_pool_noalloc", "fic_last_error", "fic_pack", "fic_server_create", "fic_server_submit",
+           "fic_domain_pool_noalloc", "fic_last_error", "fic_pack", "fic_tune_mode",
+           "fic_tune_read", "fic_server_create", "fic_server_submit",
            "fic_server_poll", "fic_server_stats_read", "fic_server_destroy"]
 
 
@@ -133,6 +140,8 @@ def lib():
                                           C.POINTER(C.c_int64), vp]
     L.fic_pack.argtypes = [vp, C.POINTER(FicParams), C.POINTER(FicResult), vp, C.c_int64,
                            C.POINTER(C.c_int64), C.POINTER(C.c_int64), vp]
+    L.fic_tune_mode.argtypes = [C.c_int, C.POINTER(C.c_int)]
+    L.fic_tune_read.argtypes = [C.POINTER(FicTuneEntry), C.c_int, C.POINTER(C.c_int)]
     L.fic_server_create.argtypes = [C.POINTER(FicParams), C.POINTER(FicServerConfig),
                                     C.POINTER(vp)]
     L.fic_server_submit.argtypes = [vp, vp, C.c_int, C.POINTER(C.c_int64)]
@@ -336,6 +345,23 @@ def fic_domain_pool(img, N, B, L, entropy_thresh, stream=None, pool_dn=0):
                                _stream(stream))
     _check(st, "fic_domain_pool")
     return xy[: dn.value].copy(), ent[:npos].copy(), int(near.value)
+
+
+def fic_tune_mode(mode=-1):
+    """Set the contraction-shape tuning mode (0 fixed, 1 measure on first
+    use, 2 + i force candidate i); returns the previous mode."""
+    prev = C.c_int(0)
+    _check(lib().fic_tune_mode(int(mode), C.byref(prev)), "fic_tune_mode")
+    return prev.value
+
+
+def fic_tune_read():
+    """The tuned classes so far (list of dicts)."""
+    n = C.c_int(0)
+    _check(lib().fic_tune_read(None, 0, C.byref(n)), "fic_tune_read")
+    arr = (FicTuneEntry * max(n.value, 1))()
+    _check(lib().fic_tune_read(arr, n.value, C.byref(n)), "fic_tune_read")
+    return [{k: getattr(arr[i], k) for k, _ in FicTuneEntry._fields_} for i in range(n.value)]
 
 
 def fic_stats_reset(timing=False):
