@@ -498,7 +498,7 @@ def run_serving(args):
     with pkg.Server(16, 4, 2, 4.0, ss, 8.0) as w:
         for side in sorted(set(int(n) for n in sides)):
             w.poll(w.submit(fic_synth.one_over_f(side, 1, 2.0)))
-    srv = pkg.Server(16, 4, 2, 4.0, ss, 8.0)
+    srv = pkg.Server(16, 4, 2, 4.0, ss, 8.0, policy=args.policy)
     tickets = [None] * len(imgs)
     sampler = ClockSampler(dev.index)
     sampler.start()
@@ -537,7 +537,8 @@ def run_serving(args):
         "dtype": "fp16->fp32 (exact int)", "data": "synthetic",
         "config": {"workload": SERVING_DESC, "arrival_span_s": float(t_arr[-1]),
                    "sides": {str(k): len(v) for k, v in sorted(by_side.items())},
-                   "server": {"hbm_budget": st["hbm_budget"], "max_inflight": 64}},
+                   "server": {"hbm_budget": st["hbm_budget"], "max_inflight": 64,
+                              "policy": ["fifo", "smallest first, 2 s aging"][args.policy]}},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
                        "p99": float(np.percentile(lat, 99)), "max": float(lat.max()),
                        "mean_queue_wait": float(wait.mean())},
@@ -632,6 +633,8 @@ def main():
                     help="precision512: the headline line; batch64: the 64-image batching "
                          "form; serving: the request server under a Poisson stream")
     ap.add_argument("--requests", type=int, default=200, help="serving: number of requests")
+    ap.add_argument("--policy", type=int, default=0, choices=[0, 1],
+                    help="serving: admission order (0 FIFO, 1 smallest image first with aging)")
     ap.add_argument("--only-side", type=int, default=0, choices=[0, 16, 8, 4],
                     help="profiling aid: encode one quadtree step at this side (all ranges)")
     args = ap.parse_args()

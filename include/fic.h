@@ -269,6 +269,10 @@ typedef struct {
     int32_t max_inflight;  /* admitted images at once (slots); 0 = 64      */
     int32_t max_queue;     /* waiting requests; 0 = 65536.  A submit
                               beyond it returns FIC_EBUSY                 */
+    int32_t policy;        /* admission order: 0 FIFO; 1 smallest image
+                              first, except that a request waiting longer
+                              than age_ms goes first (oldest first)        */
+    int32_t age_ms;        /* policy 1 aging limit; 0 = 2000 ms           */
 } fic_server_config;
 
 typedef struct {
@@ -330,19 +334,24 @@ const char* fic_strerror(int status);
  * give identical records: isometry-in-accumulator tiles (128 ranges x 64
  * pool domains x 8 isometries; 2x2 to 8x8 ranges with at most 3 S values)
  * or row tiles (128 (range, isometry) rows x 256 domains), each with a work
- * chunking tuned for a per-item refill cost of 1, 2 or 4 tiles.  In mode 1
+ * chunking tuned for a per-item refill cost of 1, 2 or 4 tiles, and for
+ * isometry tiles 8 or 16 epilogue warps.  In mode 1
  * (the default) the first step of each (engine, K = B*B padded, |S|, size
  * class = floor(log2(ranges x pool domains))) runs every candidate once on
  * its own operands, timed with CUDA events, and keeps the fastest for that
  * class (per engine: the synchronous entry points share one per device;
  * each server has its own).  Mode 0: the fixed default (isometry tiles
- * where they apply, refill 2); mode 2 + i: candidate i for every step
+ * where they apply, 8 epilogue warps, refill 2); mode 2 + i: candidate i
+ * for every step
  * (i taken modulo the step's candidate count).  The paper has no
  * counterpart; this is the GPU design's tile-shape choice. */
 typedef struct {
     int32_t engine, K, n_s, size_class;  /* the class                      */
     int32_t iso_tiles;                   /* 1: isometry tiles; 0: row tiles */
     int32_t refill;                      /* chunking refill cost, tiles     */
+    int32_t epi_warps;                   /* epilogue warps (isometry tiles:
+                                            8 with 16-column TMEM reads, or
+                                            16 with 8-column reads)        */
     float ms;                            /* measured contraction time       */
     int32_t candidates;                  /* shapes measured                 */
 } fic_tune_entry;

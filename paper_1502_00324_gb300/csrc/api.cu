@@ -488,6 +488,7 @@ int fic_tune_read(fic_tune_entry* out, int cap, int* n)
         out[i].size_class = t[(size_t)i].size_class;
         out[i].iso_tiles = t[(size_t)i].choice.iso;
         out[i].refill = t[(size_t)i].choice.refill;
+        out[i].epi_warps = t[(size_t)i].choice.iso ? (t[(size_t)i].choice.epi ? 16 : 8) : 8;
         out[i].ms = t[(size_t)i].ms;
         out[i].candidates = t[(size_t)i].candidates;
     }

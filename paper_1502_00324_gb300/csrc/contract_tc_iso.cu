@@ -37,16 +37,19 @@ using namespace tc;
 template <int K> struct IsoShape;
 template <> struct IsoShape<16> { static constexpr int N = 64, PASS = 4; };
 template <> struct IsoShape<64> { static constexpr int N = 64, PASS = 4; };
-#ifndef FIC_ISO_EPI_WARPS
-#define FIC_ISO_EPI_WARPS 8
-#endif
-constexpr int kEpiWarps = FIC_ISO_EPI_WARPS;  // 4 x (column slices per tile)
-constexpr int kThreads = 32 * (2 + kEpiWarps);
-constexpr int kPartsPerChunk = kEpiWarps / 4;  // one partial per column slice
+// Epilogue decompositions (chosen by the tuner): EPI = 8 warps reading 16
+// columns per TMEM load, or EPI = 16 warps reading 8 columns per load (more
+// warps to hide latency, fewer registers each).
+template <int EPI> struct IsoEpi {
+    static constexpr int kEpiWarps = EPI;                    // 4 x column slices
+    static constexpr int kThreads = 32 * (2 + EPI);
+    static constexpr int kPartsPerChunk = EPI / 4;           // one per column slice
+    static constexpr int kChunk = EPI == 16 ? 8 : 16;        // columns per TMEM load
+    static constexpr int kWarpsPerSubPartition = (kThreads / 32 + 3) / 4;
+    static constexpr int kMaxRegs = 16384 / (32 * kWarpsPerSubPartition) / 8 * 8;
+};
 constexpr uint32_t kTmemCols = 512;    // all of TMEM: 512 / (PASS N) slots
 constexpr int kMaxSlots = 4;
-constexpr int kWarpsPerSubPartition = (kThreads / 32 + 3) / 4;
-constexpr int kMaxRegs = 16384 / (32 * kWarpsPerSubPartition) / 8 * 8;
 
 // Launch parameters; per-image data comes from the problem table (A is
 // iso-major: row k * (rows_pad / 8) + range; gbest and partials per range).
@@ -64,16 +67,16 @@ __device__ __forceinline__ float fmax3(float a, float b, float c)
     return r;
 }
 
-template <int P>
-__device__ __forceinline__ float iso_max(const float (&x)[P][16], int i)
+template <int P, int W>
+__device__ __forceinline__ float iso_max(const float (&x)[P][W], int i)
 {
     if constexpr (P == 4) return fmaxf(fmax3(x[0][i], x[1][i], x[2][i]), x[3][i]);
     else return fmaxf(x[0][i], x[1][i]);
 }
 
 // Filter pass over 16 columns (4 groups of 4) x P isometries of one range.
-template <int NS, int P>
-__device__ __forceinline__ float iso_pass1(const float (&x)[P][16], const float* __restrict__ cf,
+template <int NS, int P, int W>
+__device__ __forceinline__ float iso_pass1(const float (&x)[P][W], const float* __restrict__ cf,
                                            int g0, float na, const StepParams& sp)
 {
     constexpr int cw = 1 + NS;
@@ -83,10 +86,10 @@ __device__ __forceinline__ float iso_pass1(const float (&x)[P][16], const float*
 #pragma unroll
     for (int s = 0; s < NS; ++s) nk[s] = pk2(-sp.kf[s], -sp.kf[s]);
 #pragma unroll
-    for (int g = 0; g < 4; ++g) {
+    for (int g = 0; g < W / 4; ++g) {
         float c[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) c[e] = iso_max<P>(x, 4 * g + e);
+        for (int e = 0; e < 4; ++e) c[e] = iso_max<P, W>(x, 4 * g + e);
         const float4* cg = reinterpret_cast<const float4*>(cf + (size_t)(g0 + g) * cw * 4);
         const float4 m = cg[0];
         const uint64_t t01 = fma2(nak, pk2(m.x, m.y), pk2(c[0], c[1]));
@@ -109,8 +112,8 @@ __device__ __forceinline__ float iso_pass1(const float (&x)[P][16], const float*
 // Candidates of one range arrive out of index order across passes, so a
 // candidate is skipped only when its lower bound proves h > h* (index below
 // the best) or h > h* - 1 (index above it).
-template <int NS, int P>
-__device__ __forceinline__ void iso_pass2(RowState& st, const float (&x)[P][16], float mn,
+template <int NS, int P, int W>
+__device__ __forceinline__ void iso_pass2(RowState& st, const float (&x)[P][W], float mn,
                                           const float* __restrict__ cf, int g0, int col_base,
                                           int iso_base, float na, float delta, float inv_n,
                                           int sr, const ColExact* __restrict__ ci, int dn,
@@ -120,11 +123,11 @@ __device__ __forceinline__ void iso_pass2(RowState& st, const float (&x)[P][16],
     constexpr int cw = 1 + NS;
     float te = fminf(st.thr, __fadd_ru(mn, 2.0f * delta));
 #pragma unroll
-    for (int g = 0; g < 4; ++g) {
+    for (int g = 0; g < W / 4; ++g) {
         const float* cg = cf + (size_t)(g0 + g) * cw * 4;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const float cmax = iso_max<P>(x, 4 * g + e);
+            const float cmax = iso_max<P, W>(x, 4 * g + e);
             float fm = __int_as_float(0x7f800000);
 #pragma unroll
             for (int s = 0; s < NS; ++s) fm = fminf(fm, col_filter(cg, e, na, cmax, sp, s));
@@ -157,6 +160,16 @@ __device__ __forceinline__ void iso_pass2(RowState& st, const float (&x)[P][16],
     }
 }
 
+// 4 x 8 columns of TMEM (4 accumulators 'stride' columns apart), one wait.
+__device__ __forceinline__ void tmem_load_iso(uint32_t taddr, uint32_t stride, float (&x)[4][8])
+{
+    tmem_ld8_issue(taddr, x[0]);
+    tmem_ld8_issue(taddr + stride, x[1]);
+    tmem_ld8_issue(taddr + 2 * stride, x[2]);
+    tmem_ld8_issue(taddr + 3 * stride, x[3]);
+    tmem_wait4x8(x[0], x[1], x[2], x[3]);
+}
+
 // P x 16 columns of TMEM (P accumulators 'stride' columns apart), one wait.
 template <int P>
 __device__ __forceinline__ void tmem_load_iso(uint32_t taddr, uint32_t stride, float (&x)[P][16])
@@ -174,10 +187,13 @@ __device__ __forceinline__ void tmem_load_iso(uint32_t taddr, uint32_t stride, f
     }
 }
 
-template <int K, int NS>
-__global__ void __maxnreg__(kMaxRegs)
+template <int K, int NS, int EPI>
+__global__ void __maxnreg__(IsoEpi<EPI>::kMaxRegs)
 contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constant__ StepParams sp)
 {
+    constexpr int kEpiWarps = IsoEpi<EPI>::kEpiWarps;
+    constexpr int kPartsPerChunk = IsoEpi<EPI>::kPartsPerChunk;
+    constexpr int kChunk = IsoEpi<EPI>::kChunk;
     static_assert(K == 16 || K == 64, "one K-block per tile");
     constexpr int kN = IsoShape<K>::N;                // pool columns per tile
     constexpr int kPass = IsoShape<K>::PASS;          // isometries per pass
@@ -396,22 +412,23 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
                     const uint32_t tb = tmem_base + ((uint32_t)(quad * 32) << 16) +
                                         (uint32_t)(slot * kSlotCols + hsel * kWarpCols);
 #pragma unroll 1
-                    for (int c16 = 0; c16 < kWarpCols / 16; ++c16) {
-                        float x[kPass][16];
+                    for (int ch = 0; ch < kWarpCols / kChunk; ++ch) {
+                        float x[kPass][kChunk];
                         __syncwarp();
-                        tmem_load_iso<kPass>(tb + 16u * c16, (uint32_t)kN, x);
-                        if (c16 == kWarpCols / 16 - 1) {
+                        tmem_load_iso(tb + (uint32_t)(kChunk * ch), (uint32_t)kN, x);
+                        if (ch == kWarpCols / kChunk - 1) {
                             // the pass is in registers: hand the slot back to the MMA
                             tc_fence_before();
                             __syncwarp();
                             if (lane == 0) mbar_arrive(tempty(slot));
                         }
                         if (valid) {
-                            const int g0 = (hsel * kWarpCols + 16 * c16) / 4;
-                            const float mn = iso_pass1<NS, kPass>(x, cfs, g0, -r.a, sp);
+                            const int g0 = (hsel * kWarpCols + kChunk * ch) / 4;
+                            const float mn = iso_pass1<NS, kPass, kChunk>(x, cfs, g0, -r.a, sp);
                             if (mn <= st.thr)
-                                iso_pass2<NS, kPass>(st, x, mn, cfs, g0, ct * kN, pass * kPass,
-                                                     -r.a, r.delta, inv_n, r.sr, qci, qdn, &sp);
+                                iso_pass2<NS, kPass, kChunk>(st, x, mn, cfs, g0, ct * kN,
+                                                             pass * kPass, -r.a, r.delta, inv_n,
+                                                             r.sr, qci, qdn, &sp);
                         }
                     }
                     if (++slot == kSlots) {
@@ -473,12 +490,12 @@ size_t iso_layout(int cw, int* nstage_out, int* ncf_out)
     return total;
 }
 
-template <int K, int NS>
+template <int K, int NS, int EPI>
 cudaError_t launch_iso_kns(const ContractArgs& a, cudaStream_t s)
 {
     int nstage = 0, ncf = 0;
     const size_t smem = iso_layout<K>(a.sp.cw, &nstage, &ncf);
-    auto kern = contract_tc_iso_kernel<K, NS>;
+    auto kern = contract_tc_iso_kernel<K, NS, EPI>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -490,25 +507,34 @@ cudaError_t launch_iso_kns(const ContractArgs& a, cudaStream_t s)
     P.nstage = nstage;
     P.ncf = ncf;
     const int grid = P.n_items < a.grid_ctas ? P.n_items : a.grid_ctas;
-    kern<<<grid, kThreads, smem, s>>>(P, a.sp);
+    kern<<<grid, IsoEpi<EPI>::kThreads, smem, s>>>(P, a.sp);
     return cudaGetLastError();
+}
+
+template <int K, int EPI>
+cudaError_t launch_iso_ke(const ContractArgs& a, cudaStream_t s)
+{
+    switch (a.sp.ns) {
+        case 1: return launch_iso_kns<K, 1, EPI>(a, s);
+        case 2: return launch_iso_kns<K, 2, EPI>(a, s);
+        case 3: return launch_iso_kns<K, 3, EPI>(a, s);
+        default: return cudaErrorInvalidValue;  // larger S sets use the row kernel
+    }
 }
 
 template <int K>
 cudaError_t launch_iso_k(const ContractArgs& a, cudaStream_t s)
 {
-    switch (a.sp.ns) {
-        case 1: return launch_iso_kns<K, 1>(a, s);
-        case 2: return launch_iso_kns<K, 2>(a, s);
-        case 3: return launch_iso_kns<K, 3>(a, s);
-        default: return cudaErrorInvalidValue;  // larger S sets use the row kernel
-    }
+    return a.variant == 1 ? launch_iso_ke<K, 16>(a, s) : launch_iso_ke<K, 8>(a, s);
 }
 
 }  // namespace
 
 bool contract_tc_iso_supports(int K, int ns) { return (K == 16 || K == 64) && ns >= 1 && ns <= 3; }
-int contract_tc_iso_parts_per_chunk() { return kPartsPerChunk; }
+int contract_tc_iso_parts_per_chunk(int variant)
+{
+    return variant == 1 ? IsoEpi<16>::kPartsPerChunk : IsoEpi<8>::kPartsPerChunk;
+}
 int contract_tc_iso_ntile(int K) { return K == 16 ? IsoShape<16>::N : IsoShape<64>::N; }
 
 cudaError_t launch_contract_tc_iso(const ContractArgs& a, cudaStream_t s)

@@ -158,6 +158,7 @@ struct StepShape {
     int64_t tile_w;      // pool columns per tile
     int parts_per_chunk; // partial bests per (range, column chunk)
     int refill;          // chunking: per-item refill cost in tiles
+    int epi;             // isometry kernel epilogue variant
 };
 
 StepShape step_shape(const fic_params& p, int lvl, const TuneChoice& v)
@@ -172,8 +173,9 @@ StepShape step_shape(const fic_params& p, int lvl, const TuneChoice& v)
     const bool tc = p.engine == FIC_ENGINE_TENSOR;
     h.iso = tc && v.iso && contract_tc_iso_supports(h.K, h.sp.ns);
     h.tile_w = h.iso ? contract_tc_iso_ntile(h.K) : (tc ? contract_tc_ntile() : kPlainNTile);
-    h.parts_per_chunk =
-        h.iso ? contract_tc_iso_parts_per_chunk() : (tc ? contract_tc_parts_per_chunk() : 1);
+    h.epi = v.epi;
+    h.parts_per_chunk = h.iso ? contract_tc_iso_parts_per_chunk(h.epi)
+                              : (tc ? contract_tc_parts_per_chunk() : 1);
     h.refill = v.refill > 0 ? v.refill : 2;
     return h;
 }
@@ -186,12 +188,15 @@ std::vector<TuneChoice> tune_candidates(const fic_params& p, int lvl)
     const bool iso_ok =
         p.engine == FIC_ENGINE_TENSOR && contract_tc_iso_supports(K, p.S_sets[lvl].n_s);
     std::vector<TuneChoice> c;
-    for (int refill : {1, 2, 4}) c.push_back(TuneChoice{iso_ok ? 1 : 0, refill});
-    if (iso_ok) c.push_back(TuneChoice{0, 2});  // the row kernel on the same step
+    for (int refill : {1, 2, 4}) c.push_back(TuneChoice{iso_ok ? 1 : 0, refill, 0});
+    if (iso_ok) {
+        c.push_back(TuneChoice{1, 2, 1});  // 16 epilogue warps, 8-column reads
+        c.push_back(TuneChoice{0, 2, 0});  // the row kernel on the same step
+    }
     return c;
 }
 
-TuneChoice default_choice() { return TuneChoice{1, 2}; }
+TuneChoice default_choice() { return TuneChoice{1, 2, 0}; }
 
 int64_t rows_pad_for(const StepShape& h, int64_t R)
 {
@@ -663,6 +668,7 @@ int Engine::step(const fic_params& p, const std::vector<Job*>& jobs, Launcher& L
         a.sp = h.sp;
         a.err = &ds[leaders[lvl]].err;
         a.grid_ctas = sm_count_;
+        a.variant = h.epi;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (ms) {
             FIC_TRY(cudaEventCreate(&e0));

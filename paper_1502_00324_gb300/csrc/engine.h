@@ -115,11 +115,13 @@ struct Job {
 };
 
 // A contraction shape choice of the tuner: kernel family (1: isometry-in-
-// accumulator tiles where they apply, 0: row tiles) and the chunking's
-// per-item refill cost in tiles.
+// accumulator tiles where they apply, 0: row tiles), the chunking's
+// per-item refill cost in tiles, and the isometry kernel's epilogue (0: 8
+// warps x 16-column TMEM reads, 1: 16 warps x 8-column reads).
 struct TuneChoice {
     int iso;
     int refill;
+    int epi;
 };
 
 // Tuning mode (process-wide): 0 fixed default shape, 1 measure on first use

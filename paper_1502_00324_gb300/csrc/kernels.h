@@ -19,6 +19,7 @@ struct ContractArgs {
     StepParams sp;
     int* err;              // device error word
     int grid_ctas;         // persistent grid size (tensor engines)
+    int variant;           // isometry kernel: 0 = 8 epilogue warps, 1 = 16
 };
 
 cudaError_t launch_contract_plain(const ContractArgs& a, cudaStream_t s);
@@ -28,7 +29,7 @@ cudaError_t launch_contract_tc(const ContractArgs& a, cudaStream_t s);
 // of 128); partials per range; gbest per range.
 cudaError_t launch_contract_tc_iso(const ContractArgs& a, cudaStream_t s);
 bool contract_tc_iso_supports(int K, int ns);
-int contract_tc_iso_parts_per_chunk();
+int contract_tc_iso_parts_per_chunk(int variant);
 int contract_tc_iso_ntile(int K);
 size_t contract_tc_smem_bytes(int K);
 int contract_tc_parts_per_chunk();  // partial bests per (range, column chunk)

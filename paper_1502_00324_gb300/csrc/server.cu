@@ -2,7 +2,8 @@
 // continuous batching of image encodes on one device.
 //
 // Worker iteration (one host thread per server, one CUDA stream):
-//   1. admission: FIFO queue -> free slot, while the estimated device bytes
+//   1. admission: queue (FIFO, or smallest image first with aging) -> free
+//      slot, while the estimated device bytes
 //      of all slots stay within the budget (slots keep their buffers between
 //      images; idle slots are emptied when room is needed);
 //   2. begin() for the images admitted now (upload, 2x2 sums, top ranges);
@@ -113,7 +114,13 @@ struct fic_server {
     void admit(std::vector<InFlight*>& fresh)
     {
         while (!queue.empty() && (int)inflight.size() < cfg.max_inflight) {
-            Request& r = queue.front();
+            // policy 1: the oldest request once it has waited age_ms, else the
+            // smallest image (earliest among equals); policy 0: the oldest
+            size_t pick = 0;
+            if (cfg.policy == 1 && now_ms() - queue.front().submit_ms < (double)cfg.age_ms)
+                for (size_t q = 1; q < queue.size(); ++q)
+                    if (queue[q].N < queue[pick].N) pick = q;
+            Request& r = queue[pick];
             int slot = -1;
             for (int k = 0; k < cfg.max_inflight; ++k) {
                 if (slot_busy[(size_t)k]) continue;
@@ -138,7 +145,7 @@ struct fic_server {
                 // larger than the whole budget: refuse this one
                 std::unique_ptr<InFlight> f(new InFlight());
                 f->req = std::move(r);
-                queue.pop_front();
+                queue.erase(queue.begin() + (std::ptrdiff_t)pick);
                 f->admit_ms = now_ms();
                 finish_one(f, FIC_ENOMEM, false);
                 continue;
@@ -148,7 +155,7 @@ struct fic_server {
             if (st.hbm_in_use > st.hbm_peak) st.hbm_peak = st.hbm_in_use;
             std::unique_ptr<InFlight> f(new InFlight());
             f->req = std::move(r);
-            queue.pop_front();
+            queue.erase(queue.begin() + (std::ptrdiff_t)pick);
             f->job.slot = slot;
             f->admit_ms = now_ms();
             slot_busy[(size_t)slot] = 1;
@@ -287,6 +294,8 @@ int fic_server_create(const fic_params* p, const fic_server_config* cfg, fic_ser
         if (cfg) s->cfg = *cfg;
         if (s->cfg.max_inflight <= 0) s->cfg.max_inflight = 64;
         if (s->cfg.max_queue <= 0) s->cfg.max_queue = 65536;
+        if (s->cfg.policy != 0 && s->cfg.policy != 1) return FIC_EINVAL;
+        if (s->cfg.age_ms <= 0) s->cfg.age_ms = 2000;
         if (s->cfg.hbm_budget <= 0) {
             size_t fr = 0, tot = 0;
             FIC_TRY(cudaMemGetInfo(&fr, &tot));

@@ -192,6 +192,28 @@ static __device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, float (&v
         : "r"(taddr));
 }
 
+// 32 lanes x 8 columns (one register per column) starting at taddr.
+static __device__ __forceinline__ void tmem_ld8_issue(uint32_t taddr, float (&v)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]),
+                   "=f"(v[6]), "=f"(v[7])
+                 : "r"(taddr));
+}
+
+// Waits for this thread's outstanding tcgen05.ld of four 8-column arrays.
+static __device__ __forceinline__ void tmem_wait4x8(float (&a)[8], float (&b)[8], float (&c)[8],
+                                             float (&d)[8])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+f"(a[0]), "+f"(a[1]), "+f"(a[2]), "+f"(a[3]), "+f"(a[4]), "+f"(a[5]), "+f"(a[6]), "+f"(a[7]),
+                   "+f"(b[0]), "+f"(b[1]), "+f"(b[2]), "+f"(b[3]), "+f"(b[4]), "+f"(b[5]), "+f"(b[6]), "+f"(b[7]),
+                   "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3]), "+f"(c[4]), "+f"(c[5]), "+f"(c[6]), "+f"(c[7]),
+                   "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3]), "+f"(d[4]), "+f"(d[5]), "+f"(d[6]), "+f"(d[7])
+                 :
+                 : "memory");
+}
+
 // Waits for this thread's outstanding tcgen05.ld of four 16-column arrays.
 static __device__ __forceinline__ void tmem_wait4x16(float (&a)[16], float (&b)[16], float (&c)[16],
                                               float (&d)[16])

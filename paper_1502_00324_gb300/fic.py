@@ -58,7 +58,8 @@ class FicParams(C.Structure):
 
 
 class FicServerConfig(C.Structure):
-    _fields_ = [("hbm_budget", C.c_int64), ("max_inflight", C.c_int32), ("max_queue", C.c_int32)]
+    _fields_ = [("hbm_budget", C.c_int64), ("max_inflight", C.c_int32), ("max_queue", C.c_int32),
+                ("policy", C.c_int32), ("age_ms", C.c_int32)]
 
 
 class FicTiming(C.Structure):
@@ -77,7 +78,7 @@ class FicServerStats(C.Structure):
 class FicTuneEntry(C.Structure):
     _fields_ = [("engine", C.c_int32), ("K", C.c_int32), ("n_s", C.c_int32),
                 ("size_class", C.c_int32), ("iso_tiles", C.c_int32), ("refill", C.c_int32),
-                ("ms", C.c_float), ("candidates", C.c_int32)]
+                ("epi_warps", C.c_int32), ("ms", C.c_float), ("candidates", C.c_int32)]
 
 
 class FicStats(C.Structure):
@@ -406,10 +407,11 @@ class Server:
     or None while the image is queued or running."""
 
     def __init__(self, B_max, B_min, L, entropy_thresh, ssets, err_tol, engine=ENGINE_TENSOR,
-                 hbm_budget=0, max_inflight=0, max_queue=0, pool_dn=0):
+                 hbm_budget=0, max_inflight=0, max_queue=0, pool_dn=0, policy=0, age_ms=0):
         self._p = make_params(B_max, B_max, B_min, L, entropy_thresh, ssets, err_tol, engine,
                               pool_dn)
-        cfg = FicServerConfig(int(hbm_budget), int(max_inflight), int(max_queue))
+        cfg = FicServerConfig(int(hbm_budget), int(max_inflight), int(max_queue), int(policy),
+                              int(age_ms))
         h = C.c_void_p()
         _check(lib().fic_server_create(C.byref(self._p), C.byref(cfg), C.byref(h)),
                "fic_server_create")

@@ -145,3 +145,24 @@ def test_destroy_with_work_pending(pkg):
     # the library is still usable afterwards
     img = fic_synth.one_over_f(64, 1, 2.0)
     assert alone(pkg, img).n_codes > 0
+
+
+def test_smallest_first_policy_with_aging(pkg):
+    """Policy 1 admits the smallest queued image first (one slot here), so
+    small requests queued behind a large one finish before it; results are
+    unchanged.  An unknown policy is rejected."""
+    big = [fic_synth.one_over_f(384, 80 + i, 2.0) for i in range(2)]
+    small = [fic_synth.one_over_f(64, 90 + i, 2.0) for i in range(3)]
+    srv = make_server(pkg, max_inflight=1, policy=1, age_ms=60000)
+    t_big0 = srv.submit(big[0])
+    t_big1 = srv.submit(big[1])
+    t_small = [srv.submit(im) for im in small]
+    res = {t: srv.poll(t) for t in [t_big0, t_big1] + t_small}
+    srv.close()
+    done = {t: tm["done_ms"] for t, (_, tm) in res.items()}
+    assert max(done[t] for t in t_small) < done[t_big1]
+    for t, im in zip([t_big0, t_big1] + t_small, big + small):
+        np.testing.assert_array_equal(res[t][0].codes, alone(pkg, im).codes)
+    with pytest.raises(pkg.FicError) as e:
+        make_server(pkg, policy=7)
+    assert e.value.status == pkg.fic.FIC_EINVAL
