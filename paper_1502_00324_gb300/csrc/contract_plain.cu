@@ -44,12 +44,18 @@ contract_plain_kernel(const Problem* __restrict__ probs, int n_probs,
     const bool valid = range < R && !range_is_flat(r, sp.n);
     const float inv_n = 1.0f / (float)sp.n;
 
+    // thresholds are per range: the 8 isometries of a thread and the 16
+    // threads of a range share theirs every tile, together with the best key
+    // other chunks of the range have published (read one tile ahead)
+    long long* const gb = gbest + range;
     RowState st[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         row_state_init(st[i]);
-        if (valid) row_state_seed(st[i], gbest + (int64_t)range * 8 + i, inv_n, r.delta);
+        if (valid) row_state_seed(st[i], gb, inv_n, r.delta);
     }
+    long long gseen = valid ? __ldcg(gb) : kNoCandidate;
+    long long gpub = kNoCandidate;
 
     const int ct0 = chunk * ctiles_per_chunk;
     const int ct1 = min(n_ctiles, ct0 + ctiles_per_chunk);
@@ -102,10 +108,28 @@ contract_plain_kernel(const Problem* __restrict__ probs, int n_probs,
                                   inv_n, r.sr, ci, dn, &sp);
             }
         }
+        float t = gseen < kNoCandidate ? thr_from_h(gseen, inv_n, r.delta) : st[0].thr;
+        long long hmin = st[0].h;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            t = fminf(t, st[i].thr);
+            hmin = min(hmin, st[i].h);
+        }
+#pragma unroll
+        for (int m = 1; m < 16; m <<= 1) t = fminf(t, __shfl_xor_sync(0xffffffffu, t, m));
+#pragma unroll
+        for (int i = 0; i < 8; ++i) st[i].thr = t;
+        if (valid) {
+            gseen = __ldcg(gb);
+            if (hmin < gpub) {
+                atomicMin(gb, hmin);
+                gpub = hmin;
+            }
+        }
     }
     if (valid)
 #pragma unroll
-        for (int i = 0; i < 8; ++i) row_state_publish(st[i], gbest + (int64_t)range * 8 + i);
+        for (int i = 0; i < 8; ++i) row_state_publish(st[i], gb);
     // best over the 8 isometries held by this thread, then over the 16 threads
     long long h = st[0].h;
     unsigned idx = st[0].idx;

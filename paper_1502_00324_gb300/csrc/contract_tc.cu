@@ -60,7 +60,7 @@ constexpr int kMaxRegs = kMaxRegsRaw > 255 ? 255 : kMaxRegsRaw;
 constexpr uint32_t kTmemCols = 512;
 
 // Launch parameters; per-image data comes from the problem table (A rows
-// are (range, isometry) pairs, row 8 range + k; gbest per row).
+// are (range, isometry) pairs, row 8 range + k; gbest per range).
 struct TcParams {
     const Problem* probs;
     int n_probs, n_items;
@@ -273,8 +273,19 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
             const bool valid = range < Q.R && !range_is_flat(r, sp.n);
             RowState st;
             row_state_init(st);
-            if (valid) row_state_seed(st, Q.gbest + row, inv_n, r.delta);
+            // thresholds are per range: the 8 isometry lanes of a range share
+            // theirs every tile, and the best key that other chunks of the
+            // range have published is read one tile ahead
+            long long* const gb = Q.gbest + range;
+            if (valid) row_state_seed(st, gb, inv_n, r.delta);
+            long long gseen = valid ? __ldcg(gb) : kNoCandidate;
+            long long gpub = kNoCandidate;
             for (int ct = ct0; ct < ct1; ++ct) {
+                if (gseen < kNoCandidate) st.thr = fminf(st.thr, thr_from_h(gseen, inv_n, r.delta));
+                st.thr = fminf(st.thr, __shfl_xor_sync(0xffffffffu, st.thr, 1));
+                st.thr = fminf(st.thr, __shfl_xor_sync(0xffffffffu, st.thr, 2));
+                st.thr = fminf(st.thr, __shfl_xor_sync(0xffffffffu, st.thr, 4));
+                if (valid) gseen = __ldcg(gb);
                 const int acc = (int)(tcount & 1);
                 const uint32_t ph = (uint32_t)((tcount >> 1) & 1);
                 const int cb = cidx;
@@ -336,6 +347,10 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
                                           &sp);
                 }
 #endif
+                if (st.h < gpub) {
+                    atomicMin(gb, st.h);
+                    gpub = st.h;
+                }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(cfe(cb));
                 ++tcount;
@@ -345,7 +360,7 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
                 }
             }
             if (!ok) break;
-            if (valid) row_state_publish(st, Q.gbest + row);
+            if (valid) row_state_publish(st, gb);
             // best over the 8 isometries of each range (lanes 8j .. 8j+7)
             long long h = st.h;
             unsigned idx = st.idx;

@@ -402,7 +402,13 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
             RowState st;
             row_state_init(st);
             if (valid) row_state_seed(st, Q.gbest + range, inv_n, r.delta);
+            // the best key other chunks of this range have published, read one
+            // tile ahead; this chunk publishes its own improvements per tile
+            long long gseen = valid ? __ldcg(Q.gbest + range) : kNoCandidate;
+            long long gpub = kNoCandidate;
             for (int ct = ct0; ct < ct1; ++ct) {
+                if (gseen < kNoCandidate) st.thr = fminf(st.thr, thr_from_h(gseen, inv_n, r.delta));
+                if (valid) gseen = __ldcg(Q.gbest + range);
                 if (!(ok = mbar_wait(cff(cidx), cphase, err, kWaitCycles))) break;
                 const float* cfs = reinterpret_cast<const float*>(sCF + (size_t)cidx * cf_bytes);
 #pragma unroll 1
@@ -437,6 +443,10 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
                     }
                 }
                 if (!ok) break;
+                if (st.h < gpub) {
+                    atomicMin(Q.gbest + range, st.h);
+                    gpub = st.h;
+                }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(cfe(cidx));
                 if (++cidx == ncf) {
