@@ -110,7 +110,7 @@ __device__ __forceinline__ long long exact_h(int cprime, int sr, int sd, int sd2
 // ---------------------------------------------------------------------------
 // One image's quadtree step inside a grouped contraction launch.  Work items
 // of problem p are item_start .. item_start + n_mtiles * n_chunks - 1, chunk
-// major (item = item_start + chunk * n_mtiles + mtile).
+// major (item_coords).
 // ---------------------------------------------------------------------------
 struct Problem {
     const __half* A;      // range operand (layout of the engine)
@@ -126,8 +126,23 @@ struct Problem {
     int n_mtiles, n_ct;   // M tiles, N tiles
     int n_chunks, per_chunk;
     int item_start;
-    int pad;
+    int diag;             // 1: M tile m starts at column chunk m * n_chunks / n_mtiles
 };
+
+// Column chunk and M tile of item 'local' of problem Q.  Items run chunk
+// major; with Q.diag each M tile's sequence starts at the chunk whose pool
+// domains lie at about the same image position as its ranges (ranges and
+// pool are both in raster order), where a range's best match tends to be,
+// so its threshold is tight from the first tiles on.
+__device__ __forceinline__ void item_coords(const Problem& Q, int local, int& chunk, int& mtile)
+{
+    mtile = local % Q.n_mtiles;
+    chunk = local / Q.n_mtiles;
+    if (Q.diag) {
+        chunk += (int)((long long)mtile * Q.n_chunks / Q.n_mtiles);
+        if (chunk >= Q.n_chunks) chunk -= Q.n_chunks;
+    }
+}
 
 __device__ __forceinline__ int find_problem(const Problem* __restrict__ probs, int n, int item)
 {

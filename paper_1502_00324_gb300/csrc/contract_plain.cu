@@ -18,9 +18,8 @@ __global__ void __launch_bounds__(256)
 contract_plain_kernel(const Problem* __restrict__ probs, int n_probs,
                       const __grid_constant__ StepParams sp)
 {
-    // one block per work item; M tiles vary fastest, so the blocks running
-    // together share one column chunk and a range's earlier chunks finish
-    // before its later ones start
+    // one block per work item; M tiles vary fastest (item_coords), so a
+    // range's earlier chunks finish before its later ones start
     const Problem& Q = probs[find_problem(probs, n_probs, (int)blockIdx.x)];
     const __half* __restrict__ A = Q.A;
     const __half* __restrict__ D = Q.D;
@@ -33,7 +32,8 @@ contract_plain_kernel(const Problem* __restrict__ probs, int n_probs,
     const int R = Q.R, dn = Q.dn, ctiles_per_chunk = Q.per_chunk, n_ctiles = Q.n_ct,
               n_chunks = Q.n_chunks;
     const int local = (int)blockIdx.x - Q.item_start;
-    const int mtile = local % Q.n_mtiles, chunk = local / Q.n_mtiles;
+    int chunk, mtile;
+    item_coords(Q, local, chunk, mtile);
     __shared__ __align__(16) int sA[16][128];
     __shared__ __align__(16) int sD[16][128];
     const int tid = threadIdx.x;

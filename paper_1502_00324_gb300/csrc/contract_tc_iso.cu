@@ -268,7 +268,8 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
         for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
             const Problem& Q = P.probs[find_problem(P.probs, P.n_probs, item)];
             const int local = item - Q.item_start;
-            const int chunk = local / Q.n_mtiles, mtile = local % Q.n_mtiles;
+            int chunk, mtile;
+            item_coords(Q, local, chunk, mtile);
             const int ct0 = chunk * Q.per_chunk;
             const int ct1 = min(Q.n_ct, ct0 + Q.per_chunk);
             const int64_t rpad = Q.rows_pad / 8;
@@ -329,7 +330,8 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
         bool ok = true;
         for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
             const Problem& Q = P.probs[find_problem(P.probs, P.n_probs, item)];
-            const int chunk = (item - Q.item_start) / Q.n_mtiles;
+            int chunk, mtile;
+            item_coords(Q, item - Q.item_start, chunk, mtile);
             const int ct0 = chunk * Q.per_chunk;
             const int ct1 = min(Q.n_ct, ct0 + Q.per_chunk);
             if (!(ok = mbar_wait_warp(a_full, (uint32_t)(icount & 1), err, kWaitCycles))) break;
@@ -390,7 +392,8 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
         for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
             const Problem& Q = P.probs[find_problem(P.probs, P.n_probs, item)];
             const int local = item - Q.item_start;
-            const int chunk = local / Q.n_mtiles, mtile = local % Q.n_mtiles;
+            int chunk, mtile;
+            item_coords(Q, local, chunk, mtile);
             const int ct0 = chunk * Q.per_chunk;
             const int ct1 = min(Q.n_ct, ct0 + Q.per_chunk);
             const ColExact* qci = Q.ci;

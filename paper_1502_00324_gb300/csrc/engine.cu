@@ -126,6 +126,11 @@ namespace {
 
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
+// Pool operands up to this size take the diagonal chunk order (item_coords):
+// concurrent work items then read different column chunks, which costs no
+// HBM traffic while the whole operand stays resident in L2.
+constexpr double kDiagMaxPoolBytes = 48.0 * 1024 * 1024;
+
 int ilog2i(int v)
 {
     int r = 0;
@@ -649,6 +654,8 @@ int Engine::step(const fic_params& p, const std::vector<Job*>& jobs, Launcher& L
             pr.n_chunks = j->n_chunks;
             pr.per_chunk = j->per_chunk;
             pr.item_start = (int)items;
+            // diagonal chunk order while the pool operand stays in L2
+            pr.diag = (double)j->cols_pad * h.K * 2.0 <= kDiagMaxPoolBytes ? 1 : 0;
             table_.push_back(pr);
             items += n_mtiles * j->n_chunks;
             flops += 2.0 * (8.0 * j->R) * (double)j->dn * h.n2;
