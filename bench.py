@@ -219,6 +219,7 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
 
     w, img, ss = workload()
+    pkg.fic_tune_mode(args.tune_mode)
     if args.only_side:
         # profiling aid: one quadtree step at side B over all (512 / B)^2 ranges
         lvl = {16: 0, 8: 1, 4: 2}[args.only_side]
@@ -371,6 +372,9 @@ def run_gpu(args):
         "gpu_launches": int(launches),
         "clocks": clocks,
         "wall_s_tensor": wall_t,
+        # contraction shapes the tuner kept: (K, isometry tiles, refill, epilogue warps, ms)
+        "tuned_shapes": [[t["K"], t["iso_tiles"], t["refill"], t["epi_warps"], round(t["ms"], 3)]
+                         for t in pkg.fic_tune_read()],
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -635,6 +639,9 @@ def main():
     ap.add_argument("--requests", type=int, default=200, help="serving: number of requests")
     ap.add_argument("--policy", type=int, default=0, choices=[0, 1],
                     help="serving: admission order (0 FIFO, 1 smallest image first with aging)")
+    ap.add_argument("--tune-mode", type=int, default=1,
+                    help="contraction shapes: 0 fixed, 1 measured on first use (default), "
+                         "2 + i candidate i (profiling aid: no tuning launches)")
     ap.add_argument("--only-side", type=int, default=0, choices=[0, 16, 8, 4],
                     help="profiling aid: encode one quadtree step at this side (all ranges)")
     args = ap.parse_args()
