@@ -339,8 +339,10 @@ const char* fic_strerror(int status);
  * (the default) the first step of each (engine, K = B*B padded, |S|, size
  * class = floor(log2(ranges x pool domains))) runs every candidate once on
  * its own operands, timed with CUDA events, and keeps the fastest for that
- * class (per engine: the synchronous entry points share one per device;
- * each server has its own).  Mode 0: the fixed default (isometry tiles
+ * class (one table per process, shared by the synchronous entry points and
+ * the servers; a server never runs the candidates itself: a class without
+ * an entry takes the nearest tuned class of the same (engine, K, |S|), else
+ * the default).  Mode 0: the fixed default (isometry tiles
  * where they apply, 8 epilogue warps, refill 2); mode 2 + i: candidate i
  * for every step
  * (i taken modulo the step's candidate count).  The paper has no
@@ -359,10 +361,31 @@ typedef struct {
 /* fic_tune_mode -- set the mode (mode >= 0) and/or read the previous one
  * (previous may be NULL; mode < 0 only reads).  Process-wide. */
 int fic_tune_mode(int mode, int* previous);
-/* fic_tune_read -- the tuned classes of the synchronous entry points'
- * engine on the current device: up to cap entries into out (host), *n the
- * total. */
+/* fic_tune_read -- the tuned classes so far: up to cap entries into out
+ * (host), *n the total. */
 int fic_tune_read(fic_tune_entry* out, int cap, int* n);
+
+/* ------------------------------------------------------------------ */
+/* Graph-captured encodes                                              */
+/* ------------------------------------------------------------------ */
+/* fic_encode, fic_encode_ex and fic_encode_batch run the whole quadtree of
+ * a call (every step of every image, Sec. 2) as one CUDA graph once the same
+ * configuration -- image sides, every parameter, the tuning mode, stage
+ * timing on or off -- has been encoded before: the first call runs the
+ * steps one by one (and tunes the contraction shapes), the next captures
+ * the steps with the shapes that call used, later ones replay the graph.
+ * Pool sizes, split counts and the contraction's work items stay in device
+ * memory (kernels are launched for the largest possible counts and read the
+ * actual ones), so the host waits once per call instead of once per step.
+ * Records are identical either way.  The library keeps the graphs of the 4
+ * most recently used configurations, each with its own device buffers.
+ *
+ * fic_graph_mode -- mode 1 (default): as above; mode 0: steps one by one
+ * always.  mode < 0 only reads; previous may be NULL.  Process-wide. */
+int fic_graph_mode(int mode, int* previous);
+/* fic_graph_counts -- graphs captured and replayed by the synchronous entry
+ * points on the current device (either pointer may be NULL). */
+int fic_graph_counts(int64_t* captures, int64_t* replays);
 
 /* ------------------------------------------------------------------ */
 /* Instrumentation                                                     */

@@ -17,6 +17,8 @@ from .fic import (  # noqa: F401
     fic_encode_batch,
     fic_encode_ex,
     fic_pack,
+    fic_graph_counts,
+    fic_graph_mode,
     fic_tune_mode,
     fic_tune_read,
     fic_stats_read,

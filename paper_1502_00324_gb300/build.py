@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfic.so")
-SOURCES = ["api.cu", "engine.cu", "stages.cu", "contract_plain.cu", "contract_tc.cu", "contract_tc_iso.cu",
+SOURCES = ["api.cu", "engine.cu", "graph.cu", "stages.cu", "contract_plain.cu", "contract_tc.cu", "contract_tc_iso.cu",
            "noalloc.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",

@@ -83,7 +83,17 @@ int encode_jobs(Context* c, int n, const uint8_t* const* imgs, const int* Ns,
                 cudaStream_t s)
 {
     Engine& E = c->eng;
-    int st = E.ensure_slots(n);
+    // a configuration encoded before replays its captured graph
+    bool used = false;
+    int st = E.encode_graph(n, imgs, Ns, p, dsts, caps, outs, s, &used);
+    if (used) {
+        if (st && st != FIC_ECAP) return st;
+        FIC_TRY(cudaStreamSynchronize(s));
+        return st;
+    }
+    if (st) return st;
+    E.reset_used();
+    st = E.ensure_slots(n);
     if (st) return st;
     Launcher L(s);
     std::vector<Job> jobs((size_t)n);
@@ -112,6 +122,7 @@ int encode_jobs(Context* c, int n, const uint8_t* const* imgs, const int* Ns,
         if (st) return st;
     }
     FIC_TRY(cudaStreamSynchronize(s));
+    E.note_config(n, Ns, p);
     return cap_status;
 }
 
@@ -472,14 +483,32 @@ int fic_tune_mode(int mode, int* previous)
     return FIC_OK;
 }
 
+int fic_graph_mode(int mode, int* previous)
+{
+    if (mode > 1) return FIC_EINVAL;
+    if (previous) *previous = graph_mode();
+    if (mode >= 0) set_graph_mode(mode);
+    return FIC_OK;
+}
+
+int fic_graph_counts(int64_t* captures, int64_t* replays)
+{
+    Context* c = nullptr;
+    int st = get_context(&c, nullptr);
+    if (st) return st;
+    std::lock_guard<std::mutex> guard(c->mu);
+    if (captures) *captures = c->eng.graph_captures();
+    if (replays) *replays = c->eng.graph_replays();
+    return FIC_OK;
+}
+
 int fic_tune_read(fic_tune_entry* out, int cap, int* n)
 {
     if (!n || cap < 0 || (cap > 0 && !out)) return FIC_EINVAL;
     Context* c = nullptr;
     int st = get_context(&c, nullptr);
     if (st) return st;
-    std::lock_guard<std::mutex> guard(c->mu);
-    const auto& t = c->eng.tuned();
+    const auto t = Engine::tuned();
     *n = (int)t.size();
     for (int i = 0; i < cap && i < (int)t.size(); ++i) {
         out[i].engine = t[(size_t)i].engine;

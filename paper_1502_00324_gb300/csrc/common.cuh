@@ -144,6 +144,18 @@ __device__ __forceinline__ void item_coords(const Problem& Q, int local, int& ch
     }
 }
 
+// Counts of a step that a graph-captured encode keeps in device memory (null
+// members: the host values passed alongside are the counts).  Grids are
+// sized for the host values, which are then upper bounds.
+struct StepCounts {
+    const uint32_t* R = nullptr;          // active ranges
+    const uint32_t* dn = nullptr;         // pool size
+    const uint32_t* n_parts = nullptr;    // partial bests per range
+    const uint32_t* code_base = nullptr;  // records emitted before this step
+};
+
+__host__ __device__ inline int64_t round_up64(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
 __device__ __forceinline__ int find_problem(const Problem* __restrict__ probs, int n, int item)
 {
     int lo = 0, hi = n - 1;

@@ -16,10 +16,12 @@ namespace fic {
 template <int K, int NS>
 __global__ void __launch_bounds__(256)
 contract_plain_kernel(const Problem* __restrict__ probs, int n_probs,
-                      const __grid_constant__ StepParams sp)
+                      const int* __restrict__ n_items_dev, const __grid_constant__ StepParams sp)
 {
     // one block per work item; M tiles vary fastest (item_coords), so a
-    // range's earlier chunks finish before its later ones start
+    // range's earlier chunks finish before its later ones start (the grid
+    // is an upper bound when the item count is in device memory)
+    if (n_items_dev && (int)blockIdx.x >= *n_items_dev) return;
     const Problem& Q = probs[find_problem(probs, n_probs, (int)blockIdx.x)];
     const __half* __restrict__ A = Q.A;
     const __half* __restrict__ D = Q.D;
@@ -155,10 +157,10 @@ static cudaError_t launch_plain_k(const ContractArgs& a, cudaStream_t s)
 {
     if (a.n_items == 0) return cudaSuccess;
     switch (a.sp.ns) {
-        case 1: contract_plain_kernel<K, 1><<<a.n_items, 256, 0, s>>>(a.probs, a.n_probs, a.sp); break;
-        case 2: contract_plain_kernel<K, 2><<<a.n_items, 256, 0, s>>>(a.probs, a.n_probs, a.sp); break;
-        case 3: contract_plain_kernel<K, 3><<<a.n_items, 256, 0, s>>>(a.probs, a.n_probs, a.sp); break;
-        default: contract_plain_kernel<K, 0><<<a.n_items, 256, 0, s>>>(a.probs, a.n_probs, a.sp); break;
+        case 1: contract_plain_kernel<K, 1><<<a.n_items, 256, 0, s>>>(a.probs, a.n_probs, a.n_items_dev, a.sp); break;
+        case 2: contract_plain_kernel<K, 2><<<a.n_items, 256, 0, s>>>(a.probs, a.n_probs, a.n_items_dev, a.sp); break;
+        case 3: contract_plain_kernel<K, 3><<<a.n_items, 256, 0, s>>>(a.probs, a.n_probs, a.n_items_dev, a.sp); break;
+        default: contract_plain_kernel<K, 0><<<a.n_items, 256, 0, s>>>(a.probs, a.n_probs, a.n_items_dev, a.sp); break;
     }
     return cudaGetLastError();
 }

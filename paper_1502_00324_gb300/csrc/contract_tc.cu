@@ -64,6 +64,7 @@ constexpr uint32_t kTmemCols = 512;
 struct TcParams {
     const Problem* probs;
     int n_probs, n_items;
+    const int* n_items_dev;  // device item count (graph-captured steps), else null
     int* err;
     int nstage, ncf;
 };
@@ -102,6 +103,7 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 + 2 * nstage + 4 + 2 * ncf + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_items = P.n_items_dev ? *P.n_items_dev : P.n_items;
     if (threadIdx.x == 0) {
         mbar_init(a_full, 1);
         mbar_init(a_empty, 1);
@@ -139,7 +141,7 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
         int sidx = 0, cidx = 0;          // ring positions of it and cfi
         uint32_t sphase = 0, cphase = 0; // and their parities
         bool ok = true;
-        for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
+        for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
             const Problem& Q = P.probs[find_problem(P.probs, P.n_probs, item)];
             const int local = item - Q.item_start;
             int chunk, mtile;
@@ -202,7 +204,7 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
         int sidx = 0;                    // D' stage ring position
         uint32_t sphase = 0;             // and its parity
         bool ok = true;
-        for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
+        for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
             const Problem& Q = P.probs[find_problem(P.probs, P.n_probs, item)];
             int chunk, mtile;
             item_coords(Q, item - Q.item_start, chunk, mtile);
@@ -259,7 +261,7 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
         int cidx = 0;                    // constants ring position
         uint32_t cphase = 0;             // and its parity
         bool ok = true;
-        for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
+        for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
             const Problem& Q = P.probs[find_problem(P.probs, P.n_probs, item)];
             const int local = item - Q.item_start;
             int chunk, mtile;
@@ -426,6 +428,7 @@ cudaError_t launch_tc_kns(const ContractArgs& a, cudaStream_t s)
     P.probs = a.probs;
     P.n_probs = a.n_probs;
     P.n_items = a.n_items;
+    P.n_items_dev = a.n_items_dev;
     P.err = a.err;
     P.nstage = nstage;
     P.ncf = ncf;

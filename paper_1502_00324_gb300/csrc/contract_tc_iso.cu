@@ -56,21 +56,16 @@ constexpr int kMaxSlots = 4;
 struct IsoParams {
     const Problem* probs;
     int n_probs, n_items;
+    const int* n_items_dev;  // device item count (graph-captured steps), else null
     int* err;
     int nstage, ncf;
 };
 
-__device__ __forceinline__ float fmax3(float a, float b, float c)
-{
-    float r;
-    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-    return r;
-}
-
 template <int P, int W>
 __device__ __forceinline__ float iso_max(const float (&x)[P][W], int i)
 {
-    if constexpr (P == 4) return fmaxf(fmax3(x[0][i], x[1][i], x[2][i]), x[3][i]);
+    // balanced tree: two independent maxima, then one (shorter dependency chain)
+    if constexpr (P == 4) return fmaxf(fmaxf(x[0][i], x[1][i]), fmaxf(x[2][i], x[3][i]));
     else return fmaxf(x[0][i], x[1][i]);
 }
 
@@ -228,6 +223,7 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
         reinterpret_cast<uint32_t*>(bars + 2 + 2 * nstage + 2 * kMaxSlots + 2 * ncf + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_items = P.n_items_dev ? *P.n_items_dev : P.n_items;
     if (threadIdx.x == 0) {
         mbar_init(a_full, 1);
         mbar_init(a_empty, 1);
@@ -265,7 +261,7 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
         int sidx = 0, cidx = 0;          // ring positions of it and cfi
         uint32_t sphase = 0, cphase = 0; // and their parities
         bool ok = true;
-        for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
+        for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
             const Problem& Q = P.probs[find_problem(P.probs, P.n_probs, item)];
             const int local = item - Q.item_start;
             int chunk, mtile;
@@ -328,7 +324,7 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
         int sidx = 0, slot = 0;          // D' stage and TMEM slot positions
         uint32_t sphase = 0, tphase = 0; // and their parities
         bool ok = true;
-        for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
+        for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
             const Problem& Q = P.probs[find_problem(P.probs, P.n_probs, item)];
             int chunk, mtile;
             item_coords(Q, item - Q.item_start, chunk, mtile);
@@ -389,7 +385,7 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
         int cidx = 0, slot = 0;          // constants ring and TMEM slot positions
         uint32_t cphase = 0, tphase = 0; // and their parities
         bool ok = true;
-        for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
+        for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
             const Problem& Q = P.probs[find_problem(P.probs, P.n_probs, item)];
             const int local = item - Q.item_start;
             int chunk, mtile;
@@ -516,6 +512,7 @@ cudaError_t launch_iso_kns(const ContractArgs& a, cudaStream_t s)
     P.probs = a.probs;
     P.n_probs = a.n_probs;
     P.n_items = a.n_items;
+    P.n_items_dev = a.n_items_dev;
     P.err = a.err;
     P.nstage = nstage;
     P.ncf = ncf;

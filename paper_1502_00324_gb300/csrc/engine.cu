@@ -15,6 +15,8 @@
 #include <cstring>
 
 #include "engine.h"
+#include "chunking.cuh"
+#include "shape.h"
 #include "kernels.h"
 
 namespace fic {
@@ -33,6 +35,14 @@ Launcher::Launcher(cudaStream_t s, bool allow_timing) : s_(s)
 void Launcher::begin(int kind)
 {
     kind_ = kind;
+    if (rec_) {
+        cur_.kind = kind;
+        cur_.a = cur_.b = nullptr;
+        if (rec_->timed && cudaEventCreate(&cur_.a) == cudaSuccess &&
+            cudaEventCreate(&cur_.b) == cudaSuccess)
+            cudaEventRecordWithFlags(cur_.a, s_, cudaEventRecordExternal);
+        return;
+    }
     if (!timing_) return;
     cur_.kind = kind;
     cudaEventCreate(&cur_.a);
@@ -42,6 +52,12 @@ void Launcher::begin(int kind)
 
 void Launcher::end(int launches, double flops, double bytes, int64_t matches)
 {
+    if (rec_) {
+        if (cur_.b) cudaEventRecordWithFlags(cur_.b, s_, cudaEventRecordExternal);
+        rec_->entries.push_back(GraphRec::Entry{kind_, launches, rec_->level, bytes, cur_.a, cur_.b});
+        cur_.a = cur_.b = nullptr;
+        return;
+    }
     {
         std::lock_guard<std::mutex> g(g_stats.mu);
         g_stats.st.launches[kind_] += launches;
@@ -52,6 +68,14 @@ void Launcher::end(int launches, double flops, double bytes, int64_t matches)
     if (!timing_) return;
     cudaEventRecord(cur_.b, s_);
     pending_.push_back(cur_);
+}
+
+GraphRec::~GraphRec()
+{
+    for (auto& e : entries) {
+        if (e.a) cudaEventDestroy(e.a);
+        if (e.b) cudaEventDestroy(e.b);
+    }
 }
 
 void Launcher::harvest()
@@ -124,13 +148,6 @@ bool is_device_ptr(const void* p)
 
 namespace {
 
-int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
-
-// Pool operands up to this size take the diagonal chunk order (item_coords):
-// concurrent work items then read different column chunks, which costs no
-// HBM traffic while the whole operand stays resident in L2.
-constexpr double kDiagMaxPoolBytes = 48.0 * 1024 * 1024;
-
 int ilog2i(int v)
 {
     int r = 0;
@@ -139,51 +156,6 @@ int ilog2i(int v)
 }
 
 bool valid_side(int b) { return b == 2 || b == 4 || b == 8 || b == 16; }
-
-StepParams make_step(const fic_sset& s, int n)
-{
-    StepParams sp;
-    memset(&sp, 0, sizeof(sp));
-    sp.n = n;
-    sp.q = s.q;
-    sp.ns = s.n_s;
-    sp.cw = 1 + s.n_s;  // m_c and one beta per S, in groups of 4 columns
-    for (int i = 0; i < s.n_s; ++i) {
-        sp.p[i] = s.p[i];
-        sp.kf[i] = (float)(8LL * s.p[i] * s.q);
-    }
-    return sp;
-}
-
-// Engine-dependent shape of one quadtree step under a tuning choice.
-struct StepShape {
-    int B, n2, K;
-    StepParams sp;
-    bool iso;            // isometry-in-accumulator tensor kernel
-    int64_t tile_w;      // pool columns per tile
-    int parts_per_chunk; // partial bests per (range, column chunk)
-    int refill;          // chunking: per-item refill cost in tiles
-    int epi;             // isometry kernel epilogue variant
-};
-
-StepShape step_shape(const fic_params& p, int lvl, const TuneChoice& v)
-{
-    StepShape h;
-    h.B = p.B_max >> lvl;
-    h.n2 = h.B * h.B;
-    h.K = k_pad(h.n2);
-    h.sp = make_step(p.S_sets[lvl], h.n2);
-    // isometry-in-accumulator kernel: ranges in TMEM lanes, one accumulator
-    // per isometry (iso-major A); row kernel: rows are (range, isometry)
-    const bool tc = p.engine == FIC_ENGINE_TENSOR;
-    h.iso = tc && v.iso && contract_tc_iso_supports(h.K, h.sp.ns);
-    h.tile_w = h.iso ? contract_tc_iso_ntile(h.K) : (tc ? contract_tc_ntile() : kPlainNTile);
-    h.epi = v.epi;
-    h.parts_per_chunk = h.iso ? contract_tc_iso_parts_per_chunk(h.epi)
-                              : (tc ? contract_tc_parts_per_chunk() : 1);
-    h.refill = v.refill > 0 ? v.refill : 2;
-    return h;
-}
 
 // The shapes the tuner tries for a step (all give identical records).
 std::vector<TuneChoice> tune_candidates(const fic_params& p, int lvl)
@@ -201,78 +173,21 @@ std::vector<TuneChoice> tune_candidates(const fic_params& p, int lvl)
     return c;
 }
 
-TuneChoice default_choice() { return TuneChoice{1, 2, 0}; }
-
-int64_t rows_pad_for(const StepShape& h, int64_t R)
-{
-    return h.iso ? 8 * round_up(R, 128) : round_up(8 * R, kMTile);
-}
-
-int64_t mtiles_for(const StepShape& h, int64_t rows_pad)
-{
-    return h.iso ? rows_pad / 8 / 128 : rows_pad / kMTile;
-}
-
-// Column chunking of the contraction: work items are (M tile, chunk of
-// column tiles).  Chunk counts stay <= 16 x SMs / M tiles, which bounds the
-// partial-best buffers.
-int64_t max_chunks(int sm_count, int64_t n_mtiles, int64_t n_ct)
-{
-    int64_t cap = (16LL * sm_count + n_mtiles - 1) / n_mtiles;
-    if (cap > 4096) cap = 4096;
-    if (cap > n_ct) cap = n_ct;
-    return cap < 1 ? 1 : cap;
-}
-
-// A problem alone in its launch: the chunk count that minimises the
-// estimated makespan over one item per SM (waves x tiles per item, plus a
-// per-item cost of refilling the pipeline, refill tiles).
-void choose_chunks_alone(int sm_count, int64_t n_mtiles, int64_t n_ct, int refill,
-                         int* n_chunks, int* per_chunk)
-{
-    const int64_t slots = sm_count;
-    const double item_cost = (double)refill;  // in tiles
-    int64_t best_nc = 1;
-    double best = 1e300;
-    const int64_t max_nc = max_chunks(sm_count, n_mtiles, n_ct);
-    for (int64_t nc = 1; nc <= max_nc; ++nc) {
-        const int64_t per = (n_ct + nc - 1) / nc;
-        const int64_t ncs = (n_ct + per - 1) / per;
-        if (ncs != nc) continue;
-        const int64_t waves = (n_mtiles * nc + slots - 1) / slots;
-        const double cost = (double)waves * ((double)per + item_cost);
-        if (cost < best - 1e-9) {
-            best = cost;
-            best_nc = nc;
-        }
-    }
-    *n_chunks = (int)best_nc;
-    *per_chunk = (int)((n_ct + best_nc - 1) / best_nc);
-}
-
-// Several problems in one launch: items of about tiles_per_item column
-// tiles (total tiles / (16 / refill x SMs)), so the persistent CTAs stay
-// balanced.
-void choose_chunks_shared(int sm_count, int64_t n_mtiles, int64_t n_ct, double tiles_per_item,
-                          int* n_chunks, int* per_chunk)
-{
-    int64_t per = (int64_t)(tiles_per_item + 0.5);
-    if (per < 1) per = 1;
-    if (per > n_ct) per = n_ct;
-    int64_t nc = (n_ct + per - 1) / per;
-    const int64_t cap = max_chunks(sm_count, n_mtiles, n_ct);
-    if (nc > cap) nc = cap;
-    per = (n_ct + nc - 1) / nc;
-    nc = (n_ct + per - 1) / per;
-    *n_chunks = (int)nc;
-    *per_chunk = (int)per;
-}
-
 }  // namespace
 
 int positions_per_axis(int N, int B, int L) { return (N >= 2 * B) ? (N - 2 * B) / L + 1 : 0; }
 
 static std::atomic<int> g_tune_mode{1};
+// tuned shapes of the process (one device per process)
+static std::mutex g_tune_mu;
+static std::vector<Engine::TuneEntry> g_tuned;
+
+std::vector<Engine::TuneEntry> Engine::tuned()
+{
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    return g_tuned;
+}
+
 int tune_mode() { return g_tune_mode.load(); }
 void set_tune_mode(int mode) { g_tune_mode.store(mode); }
 
@@ -304,6 +219,7 @@ int validate_params(const fic_params* p, int N, int* n_levels)
 // ---------------------------------------------------------------------------
 Engine::~Engine()
 {
+    drop_plans();
     for (auto& w : work_) w->release();
     entT_.release();
     scal_.release();
@@ -422,9 +338,15 @@ int Engine::begin(Job& job, int slot, const uint8_t* img, int N, const fic_param
 int Engine::launch_pool(Job& j, int B, int L_step, double thr, int64_t top, bool want_H,
                         Launcher& L, cudaStream_t s)
 {
-    ImageWork* w = work_[(size_t)j.slot].get();
-    Scalars* ds = scal_.as<Scalars>() + j.slot;
-    const int per = positions_per_axis(j.N, B, L_step);
+    return pool_launches(work_[(size_t)j.slot].get(), scal_.as<Scalars>() + j.slot,
+                         entT_.as<long long>(), j.dimg, j.N, B, L_step, thr, top, want_H, L, s);
+}
+
+int pool_launches(ImageWork* w, Scalars* ds, const long long* entT, const uint8_t* dimg, int N,
+                  int B, int L_step, double thr, int64_t top, bool want_H, Launcher& L,
+                  cudaStream_t s)
+{
+    const int per = positions_per_axis(N, B, L_step);
     const int64_t npos = (int64_t)per * per;
     FIC_TRY(cudaMemsetAsync(&ds->near, 0, sizeof(unsigned long long), s));
     if (npos == 0) {
@@ -440,7 +362,7 @@ int Engine::launch_pool(Job& j, int B, int L_step, double thr, int64_t top, bool
     if (top > 0) FIC_TRY(w->keys.ensure(sizeof(unsigned long long) * npos));
     if (select) FIC_TRY(w->sel.ensure(select_state_bytes()));
     L.begin(FIC_K_ENTROPY);
-    FIC_TRY(launch_entropy(j.dimg, j.N, B, L_step, per, thr, entT_.as<long long>(),
+    FIC_TRY(launch_entropy(dimg, N, B, L_step, per, thr, entT,
                            w->flags.as<uint32_t>(), want_H ? w->H.as<double>() : nullptr,
                            top > 0 ? w->keys.as<unsigned long long>() : nullptr, &ds->near, s));
     int nl = 1;
@@ -548,13 +470,23 @@ int Engine::step(const fic_params& p, const std::vector<Job*>& jobs, Launcher& L
             if (mode >= 2) {
                 choice[lvl] = cand[(size_t)(mode - 2) % cand.size()];
             } else if (mode == 1 && cand.size() > 1) {
-                trial[lvl] = true;
-                for (const TuneEntry& t : tuned_)
-                    if (t.engine == tkey[lvl][0] && t.K == tkey[lvl][1] && t.ns == tkey[lvl][2] &&
-                        t.size_class == tkey[lvl][3]) {
-                        choice[lvl] = t.choice;
-                        trial[lvl] = false;
+                // the class's tuned shape; without one, measure the candidates
+                // (synchronous entry points) or take the tuned shape of the
+                // nearest size class, else the default (the request server,
+                // whose steps must not wait for tuning runs)
+                int near_d = 1 << 30;
+                bool exact = false;
+                for (const TuneEntry& t : tuned())
+                    if (t.engine == tkey[lvl][0] && t.K == tkey[lvl][1] && t.ns == tkey[lvl][2]) {
+                        const int d = std::abs(t.size_class - tkey[lvl][3]);
+                        if (d < near_d) {
+                            near_d = d;
+                            choice[lvl] = t.choice;
+                            exact = d == 0;
+                        }
                     }
+                trial[lvl] = !exact && allow_trials_;
+                if (!exact && allow_trials_) choice[lvl] = default_choice();
             }
         }
     }
@@ -742,7 +674,10 @@ int Engine::step(const fic_params& p, const std::vector<Job*>& jobs, Launcher& L
             t.choice = best;
             t.ms = best_ms;
             t.candidates = (int)cand.size();
-            tuned_.push_back(t);
+            {
+                std::lock_guard<std::mutex> g(g_tune_mu);
+                g_tuned.push_back(t);
+            }
             choice[lvl] = best;
             const StepShape h = step_shape(p, lvl, best);
             if (h.iso != layout_iso)
@@ -757,6 +692,8 @@ int Engine::step(const fic_params& p, const std::vector<Job*>& jobs, Launcher& L
             st = run_group(lvl, step_shape(p, lvl, choice[lvl]), nullptr);
             if (st) return st;
         }
+        used_choice_[lvl] = choice[lvl];
+        used_valid_[lvl] = true;
     }
 
     // split / requeue

@@ -12,8 +12,10 @@
 #pragma once
 
 #include <cstdint>
+#include <map>
 #include <memory>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -34,9 +36,26 @@ struct StatsState {
 };
 extern StatsState g_stats;
 
+// The stages recorded while a graph is captured: launches, bytes and (when
+// timed) the external events around each stage, replayed into fic_stats
+// after every launch of the graph (graph.cu).
+struct GraphRec {
+    struct Entry {
+        int kind, launches, level;
+        double bytes;
+        cudaEvent_t a, b;
+    };
+    bool timed = false;
+    int level = -1;  // quadtree step being captured
+    std::vector<Entry> entries;
+    ~GraphRec();
+};
+
 class Launcher {
 public:
     explicit Launcher(cudaStream_t s, bool allow_timing = true);
+    // capture mode: stages go to rec instead of fic_stats
+    Launcher(cudaStream_t s, GraphRec* rec) : s_(s), rec_(rec) {}
     ~Launcher() { harvest(); }
     void begin(int kind);
     void end(int launches, double flops = 0.0, double bytes = 0.0, int64_t matches = 0);
@@ -52,6 +71,7 @@ private:
     int kind_ = FIC_K_MISC;
     Pending cur_{};
     std::vector<Pending> pending_;
+    GraphRec* rec_ = nullptr;
 };
 
 // Last CUDA error text of this thread (fic_last_error).
@@ -85,6 +105,14 @@ struct Scalars {
     unsigned long long vd_min_key;  // pool's smallest (Vd, index) key
     int err;                        // contraction error words (err, err + 1)
     int err2;
+    // device-side step state of a graph-captured encode (graph.cu)
+    uint32_t R;                     // active ranges at the current step
+    uint32_t dn;                    // pool size of the current step
+    uint32_t n_codes;               // records emitted so far
+    uint32_t n_parts;               // partial bests per range of the current step
+    uint32_t lvl_R[FIC_MAX_LEVELS];
+    uint32_t lvl_dn[FIC_MAX_LEVELS];
+    unsigned long long lvl_near[FIC_MAX_LEVELS];
 };
 
 // Device workspaces of one slot (kept and grown across jobs).
@@ -128,6 +156,10 @@ struct TuneChoice {
 // (default), 2 + i force candidate i (tests).
 int tune_mode();
 void set_tune_mode(int mode);
+// Graph mode (process-wide): 0 eager only; 1 (default) a configuration's
+// first encode runs eagerly, later ones replay its captured graph.
+int graph_mode();
+void set_graph_mode(int mode);
 
 int validate_params(const fic_params* p, int N, int* n_levels);
 int positions_per_axis(int N, int B, int L);
@@ -177,7 +209,21 @@ public:
         float ms;
         int candidates;
     };
-    const std::vector<TuneEntry>& tuned() const { return tuned_; }
+    // process-wide (every engine of the process shares the table)
+    static std::vector<TuneEntry> tuned();
+    // false: never run tuning trials inside step() (request server)
+    void set_trials(bool allow) { allow_trials_ = allow; }
+
+    // Graph-captured encodes (graph.cu).  encode_graph sets *used when it
+    // encoded the images (the configuration was encoded eagerly before:
+    // note_config after that eager encode records the shapes it used).
+    int encode_graph(int n, const uint8_t* const* imgs, const int* Ns, const fic_params& p,
+                     fic_code* const* dsts, const int64_t* caps, fic_result* outs,
+                     cudaStream_t s, bool* used);
+    void reset_used();
+    void note_config(int n, const int* Ns, const fic_params& p);
+    int64_t graph_captures() const { return graph_captures_; }
+    int64_t graph_replays() const { return graph_replays_; }
 
 private:
     int launch_pool(Job& j, int B, int L_step, double thr, int64_t top, bool want_H,
@@ -189,9 +235,31 @@ private:
     int scal_cap_ = 0;
     std::vector<std::unique_ptr<ImageWork>> work_;
     std::vector<Problem> table_;
-    std::vector<TuneEntry> tuned_;
+    bool allow_trials_ = true;
+    // shapes the last eager encode used per step
+    TuneChoice used_choice_[FIC_MAX_LEVELS] = {};
+    bool used_valid_[FIC_MAX_LEVELS] = {};
+    struct Seen {
+        TuneChoice choice[FIC_MAX_LEVELS];
+        bool no_graph = false;  // capture failed: this configuration stays eager
+    };
+    struct GraphPlan;
+    static constexpr size_t kMaxPlans = 4;
+    std::map<std::string, Seen> seen_;
+    std::vector<GraphPlan*> plans_;
+    uint64_t plan_clock_ = 0;
+    int64_t graph_captures_ = 0, graph_replays_ = 0;
+    int graph_build(GraphPlan& G, cudaStream_t s);
+    void drop_plans();
 };
 
 bool is_device_ptr(const void* p);
+
+// Pool of one step: entropy -> flags (threshold rule, or the top-DN keys and
+// a radix select) -> scan (size into ds->total) -> raster-order list in
+// w->pool.  Buffers of w grow as needed.
+int pool_launches(ImageWork* w, Scalars* ds, const long long* entT, const uint8_t* dimg, int N,
+                  int B, int L_step, double thr, int64_t top, bool want_H, Launcher& L,
+                  cudaStream_t s);
 
 }  // namespace fic

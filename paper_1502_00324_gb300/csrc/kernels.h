@@ -14,7 +14,9 @@ namespace fic {
 struct ContractArgs {
     const Problem* probs;  // n_probs entries (device)
     int n_probs;
-    int n_items;           // total work items (sum over problems)
+    int n_items;           // total work items (sum over problems); with
+                           // n_items_dev an upper bound (grid size)
+    const int* n_items_dev = nullptr;  // device item count of a graph-captured step
     int K;                 // 16, 64 or 256
     StepParams sp;
     int* err;              // device error word
@@ -55,10 +57,12 @@ cudaError_t launch_top_select(const unsigned long long* keys, int64_t n, int64_t
                               cudaStream_t s, int* launches);
 cudaError_t launch_fill_u32(uint32_t* a, int64_t n, uint32_t v, cudaStream_t s);
 // Exclusive scan of n uint32 values; *total receives the sum.  tmp holds at
-// least scan_tmp_words(n) words.
+// least scan_tmp_words(n) words.  n_dev (optional, device): scan min(n,
+// *n_dev) values instead (grids stay sized for n).
 int64_t scan_tmp_words(int64_t n);
 cudaError_t launch_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp,
-                        uint32_t* total, cudaStream_t s, int* launches);
+                        uint32_t* total, cudaStream_t s, int* launches,
+                        const uint32_t* n_dev = nullptr);
 cudaError_t launch_pool_scatter(const uint32_t* flags, const uint32_t* pos, int64_t n_pos,
                                 int per, int L, uint32_t* pool_xy, cudaStream_t s);
 // Top-level ranges (x | y << 16) of a tops x tops grid of B_max blocks.
@@ -69,23 +73,24 @@ cudaError_t launch_gather(const uint16_t* s2img, int N, int B, int L, int per,
                           const uint32_t* pool_xy, int64_t dn, int64_t cols_pad, int K,
                           const StepParams& sp, __half* D, float* cf, ColExact* ci,
                           unsigned long long* vd_max, unsigned long long* vd_min_key,
-                          cudaStream_t s);
+                          cudaStream_t s, const uint32_t* dn_dev = nullptr);
 // iso_major = 0: row 8 range + k; 1: row k * (rows_pad / 8) + range.
 cudaError_t launch_range_prep(const uint8_t* img, int N, int B, const uint32_t* act, int R,
                               int64_t rows_pad, int K, const StepParams& sp,
                               const unsigned long long* vd_max, int iso_major, __half* A,
-                              RowConst* rc, cudaStream_t s);
+                              RowConst* rc, cudaStream_t s, const uint32_t* R_dev = nullptr);
 cudaError_t launch_split_decide(const Best* part, int n_chunks, const RowConst* rc, int R,
                                 int n, const StepParams& sp, int e16, int last, int dn,
                                 const unsigned long long* vd_min_key, Best* best,
-                                uint32_t* split, cudaStream_t s);
+                                uint32_t* split, cudaStream_t s, const StepCounts& dc = {});
 cudaError_t launch_split_scatter(const uint32_t* act, const Best* best, const uint32_t* split,
                                  const uint32_t* split_pos, const RowConst* rc, int R, int B,
                                  int level, const uint32_t* pool_xy, int per, int L, int dn,
                                  uint32_t* next_act, void* codes, int64_t code_base,
-                                 cudaStream_t s);
+                                 cudaStream_t s, const StepCounts& dc = {});
 cudaError_t launch_order_mark(const void* codes, int64_t n_codes, int N, int B_max, int B_min,
-                              uint32_t* cellmap, uint32_t* cellflag, cudaStream_t s);
+                              uint32_t* cellmap, uint32_t* cellflag, cudaStream_t s,
+                              const uint32_t* n_dev = nullptr);
 cudaError_t launch_order_gather(const void* codes, const uint32_t* cellmap,
                                 const uint32_t* cellflag, const uint32_t* rank, int64_t n_cells,
                                 void* out, cudaStream_t s);

@@ -302,6 +302,7 @@ int fic_server_create(const fic_params* p, const fic_server_config* cfg, fic_ser
             s->cfg.hbm_budget = (int64_t)(fr / 2);
         }
         FIC_TRY(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+        s->eng.set_trials(false);
         int st = s->eng.init(s->stream);
         if (st == FIC_OK) st = s->eng.ensure_slots(s->cfg.max_inflight);
         if (st) {

@@ -262,9 +262,18 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total)
     return res;
 }
 
-__global__ void __launch_bounds__(kScanThreads)
-scan_reduce_kernel(const uint32_t* __restrict__ in, int64_t n, uint32_t* __restrict__ sums)
+// n_dev (optional): the count in device memory, at most n (graph-captured
+// steps size their grids for n and read the actual count here).
+__device__ __forceinline__ int64_t dev_count(int64_t n, const uint32_t* n_dev)
 {
+    return n_dev ? min(n, (int64_t)*n_dev) : n;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+scan_reduce_kernel(const uint32_t* __restrict__ in, int64_t n, const uint32_t* __restrict__ n_dev,
+                   uint32_t* __restrict__ sums)
+{
+    n = dev_count(n, n_dev);
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
     uint32_t s = 0;
     for (int i = threadIdx.x; i < kScanTile; i += kScanThreads) {
@@ -301,8 +310,9 @@ scan_top_kernel(uint32_t* __restrict__ sums, int nb, uint32_t* __restrict__ tota
 
 __global__ void __launch_bounds__(kScanThreads)
 scan_apply_kernel(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int64_t n,
-                  const uint32_t* __restrict__ sums)
+                  const uint32_t* __restrict__ n_dev, const uint32_t* __restrict__ sums)
 {
+    n = dev_count(n, n_dev);
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
     uint32_t v[kScanItems];
     uint32_t s = 0;
@@ -324,14 +334,14 @@ scan_apply_kernel(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, i
 int64_t scan_tmp_words(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
 
 cudaError_t launch_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp,
-                        uint32_t* total, cudaStream_t s, int* launches)
+                        uint32_t* total, cudaStream_t s, int* launches, const uint32_t* n_dev)
 {
     if (n <= 0) return cudaMemsetAsync(total, 0, sizeof(uint32_t), s);
     const int64_t nb = (n + kScanTile - 1) / kScanTile;
     if (nb > 4096) return cudaErrorInvalidValue;
-    scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, tmp);
+    scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, n_dev, tmp);
     scan_top_kernel<<<1, 1024, 0, s>>>(tmp, (int)nb, total);
-    scan_apply_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, tmp);
+    scan_apply_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, n_dev, tmp);
     if (launches) *launches += 3;
     return cudaGetLastError();
 }
@@ -460,14 +470,20 @@ template <int K>
 __global__ void __launch_bounds__(256)
 gather_kernel(const uint16_t* __restrict__ box, int N, int B, int L, int per,
               const uint32_t* __restrict__ pool_xy, int64_t dn, int64_t cols_pad,
-              StepParams sp, __half* __restrict__ D, float* __restrict__ cf,
-              ColExact* __restrict__ ci)
+              const uint32_t* __restrict__ dn_dev, StepParams sp, __half* __restrict__ D,
+              float* __restrict__ cf, ColExact* __restrict__ ci)
 {
     constexpr int G = K / 8;
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t c = gid / G;
     const int kg = (int)(gid % G);
-    if (c >= cols_pad) return;  // cols_pad * G is a multiple of 256: whole warps
+    // columns used: the padded pool (cols_pad stays the layout's stride)
+    int64_t cols = cols_pad;
+    if (dn_dev) {
+        dn = dev_count(dn, dn_dev);
+        cols = min(cols_pad, round_up64(dn > 0 ? dn : 1, kColPad));
+    }
+    if (c >= cols) return;  // cols * G is a multiple of 256: whole warps
     const bool real = c < dn;
     int x = 0, y = 0;
     if (real) {
@@ -526,10 +542,11 @@ gather_kernel(const uint16_t* __restrict__ box, int N, int B, int L, int per,
 // (Vd << 24 | c) of the smallest Vd (first index on ties; Vd < 2^36,
 // c < 2^24).  Grid-stride; one atomic per block.
 __global__ void __launch_bounds__(256)
-pool_stats_kernel(const ColExact* __restrict__ ci, int64_t dn, int n,
-                  unsigned long long* __restrict__ vd_max,
+pool_stats_kernel(const ColExact* __restrict__ ci, int64_t dn, const uint32_t* __restrict__ dn_dev,
+                  int n, unsigned long long* __restrict__ vd_max,
                   unsigned long long* __restrict__ vd_min_key)
 {
+    dn = dev_count(dn, dn_dev);
     unsigned long long mx = 0, mn = ~0ull;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < dn;
          c += (int64_t)gridDim.x * blockDim.x) {
@@ -568,22 +585,22 @@ cudaError_t launch_gather(const uint16_t* s2img, int N, int B, int L, int per,
                           const uint32_t* pool_xy, int64_t dn, int64_t cols_pad, int K,
                           const StepParams& sp, __half* D, float* cf, ColExact* ci,
                           unsigned long long* vd_max, unsigned long long* vd_min_key,
-                          cudaStream_t s)
+                          cudaStream_t s, const uint32_t* dn_dev)
 {
     const int64_t threads = cols_pad * (K / 8);
     const unsigned blocks = (unsigned)((threads + 255) / 256);
     switch (K) {
         case 16:
             gather_kernel<16><<<blocks, 256, 0, s>>>(s2img, N, B, L, per, pool_xy, dn, cols_pad,
-                                                     sp, D, cf, ci);
+                                                     dn_dev, sp, D, cf, ci);
             break;
         case 64:
             gather_kernel<64><<<blocks, 256, 0, s>>>(s2img, N, B, L, per, pool_xy, dn, cols_pad,
-                                                     sp, D, cf, ci);
+                                                     dn_dev, sp, D, cf, ci);
             break;
         case 256:
             gather_kernel<256><<<blocks, 256, 0, s>>>(s2img, N, B, L, per, pool_xy, dn, cols_pad,
-                                                      sp, D, cf, ci);
+                                                      dn_dev, sp, D, cf, ci);
             break;
         default: return cudaErrorInvalidValue;
     }
@@ -591,7 +608,7 @@ cudaError_t launch_gather(const uint16_t* s2img, int N, int B, int L, int per,
     if (e != cudaSuccess) return e;
     // pool-wide max Vd (filter bound) and (min Vd, first index) key (flat ranges)
     if (dn > 0) {
-        pool_stats_kernel<<<256, 256, 0, s>>>(ci, dn, B * B, vd_max, vd_min_key);
+        pool_stats_kernel<<<256, 256, 0, s>>>(ci, dn, dn_dev, B * B, vd_max, vd_min_key);
     }
     return cudaGetLastError();
 }
@@ -603,13 +620,19 @@ cudaError_t launch_gather(const uint16_t* s2img, int N, int B, int L, int per,
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
 range_prep_kernel(const uint8_t* __restrict__ img, int N, int B, const uint32_t* __restrict__ act,
-                  int R, int Rpad, int64_t rows_pad, int K, StepParams sp,
-                  const unsigned long long* __restrict__ vd_max, int iso_major,
+                  int R, const uint32_t* __restrict__ R_dev, int Rpad, int64_t rows_pad, int K,
+                  StepParams sp, const unsigned long long* __restrict__ vd_max, int iso_major,
                   __half* __restrict__ A, RowConst* __restrict__ rc)
 {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int rho = blockIdx.x * 8 + w;
-    if (rho >= Rpad) return;
+    int rlim = Rpad;
+    if (R_dev) {
+        // ranges in use: up to the M tiles that cover the R active ones
+        R = (int)dev_count(R, R_dev);
+        rlim = min(Rpad, (int)round_up64(R, 128));
+    }
+    if (rho >= rlim) return;
     const int n = B * B, G = K / 8;
     const bool real = rho < R;
     int rx = 0, ry = 0;
@@ -671,12 +694,12 @@ range_prep_kernel(const uint8_t* __restrict__ img, int N, int B, const uint32_t*
 cudaError_t launch_range_prep(const uint8_t* img, int N, int B, const uint32_t* act, int R,
                               int64_t rows_pad, int K, const StepParams& sp,
                               const unsigned long long* vd_max, int iso_major, __half* A,
-                              RowConst* rc, cudaStream_t s)
+                              RowConst* rc, cudaStream_t s, const uint32_t* R_dev)
 {
     const int Rpad = (int)(rows_pad / 8);
     if (Rpad == 0) return cudaSuccess;
-    range_prep_kernel<<<(Rpad + 7) / 8, 256, 0, s>>>(img, N, B, act, R, Rpad, rows_pad, K, sp,
-                                                     vd_max, iso_major, A, rc);
+    range_prep_kernel<<<(Rpad + 7) / 8, 256, 0, s>>>(img, N, B, act, R, R_dev, Rpad, rows_pad, K,
+                                                     sp, vd_max, iso_major, A, rc);
     return cudaGetLastError();
 }
 
@@ -690,9 +713,13 @@ __global__ void split_decide_kernel(const Best* __restrict__ part, int n_chunks,
                                     const RowConst* __restrict__ rc, int R, int n, StepParams sp,
                                     int e16, int last, int dn,
                                     const unsigned long long* __restrict__ vd_min_key,
-                                    Best* __restrict__ best, uint32_t* __restrict__ split)
+                                    Best* __restrict__ best, uint32_t* __restrict__ split,
+                                    StepCounts dc)
 {
     const int rho = blockIdx.x * blockDim.x + threadIdx.x;
+    if (dc.R) R = (int)dev_count(R, dc.R);
+    if (dc.dn) dn = (int)dev_count(dn, dc.dn);
+    if (dc.n_parts) n_chunks = (int)*dc.n_parts;
     if (rho >= R) return;
     const RowConst r = rc[rho];
     long long h = kNoCandidate;
@@ -746,9 +773,12 @@ __global__ void split_scatter_kernel(const uint32_t* __restrict__ act, const Bes
                                      const RowConst* __restrict__ rc, int R, int B, int level,
                                      const uint32_t* __restrict__ pool_xy, int per, int L, int dn,
                                      uint32_t* __restrict__ next_act, fic_code* __restrict__ codes,
-                                     int64_t code_base)
+                                     int64_t code_base, StepCounts dc)
 {
     const int rho = blockIdx.x * blockDim.x + threadIdx.x;
+    if (dc.R) R = (int)dev_count(R, dc.R);
+    if (dc.dn) dn = (int)dev_count(dn, dc.dn);
+    if (dc.code_base) code_base = *dc.code_base;
     if (rho >= R) return;
     const uint32_t v = act[rho];
     const uint32_t x = v & 0xffffu, y = v >> 16;
@@ -795,11 +825,11 @@ __global__ void split_scatter_kernel(const uint32_t* __restrict__ act, const Bes
 cudaError_t launch_split_decide(const Best* part, int n_chunks, const RowConst* rc, int R,
                                 int n, const StepParams& sp, int e16, int last, int dn,
                                 const unsigned long long* vd_min_key, Best* best,
-                                uint32_t* split, cudaStream_t s)
+                                uint32_t* split, cudaStream_t s, const StepCounts& dc)
 {
     if (R == 0) return cudaSuccess;
     split_decide_kernel<<<(R + 255) / 256, 256, 0, s>>>(part, n_chunks, rc, R, n, sp, e16, last,
-                                                        dn, vd_min_key, best, split);
+                                                        dn, vd_min_key, best, split, dc);
     return cudaGetLastError();
 }
 
@@ -807,12 +837,12 @@ cudaError_t launch_split_scatter(const uint32_t* act, const Best* best, const ui
                                  const uint32_t* split_pos, const RowConst* rc, int R, int B,
                                  int level, const uint32_t* pool_xy, int per, int L, int dn,
                                  uint32_t* next_act, void* codes, int64_t code_base,
-                                 cudaStream_t s)
+                                 cudaStream_t s, const StepCounts& dc)
 {
     if (R == 0) return cudaSuccess;
     split_scatter_kernel<<<(R + 255) / 256, 256, 0, s>>>(
         act, best, split, split_pos, rc, R, B, level, pool_xy, per, L, dn, next_act,
-        static_cast<fic_code*>(codes), code_base);
+        static_cast<fic_code*>(codes), code_base, dc);
     return cudaGetLastError();
 }
 
@@ -832,12 +862,12 @@ __device__ __forceinline__ uint32_t spread_bits(uint32_t v)
     return v;
 }
 
-__global__ void order_mark_kernel(const fic_code* __restrict__ codes, int64_t n_codes, int N,
-                                  int B_max, int B_min, uint32_t* __restrict__ cellmap,
-                                  uint32_t* __restrict__ cellflag)
+__global__ void order_mark_kernel(const fic_code* __restrict__ codes, int64_t n_codes,
+                                  const uint32_t* __restrict__ n_dev, int N, int B_max, int B_min,
+                                  uint32_t* __restrict__ cellmap, uint32_t* __restrict__ cellflag)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_codes) return;
+    if (i >= dev_count(n_codes, n_dev)) return;
     const fic_code c = codes[i];
     const int cpt = B_max / B_min;  // finest cells per top-level side
     const int cx = c.rx / B_min, cy = c.ry / B_min;
@@ -861,11 +891,12 @@ __global__ void order_gather_kernel(const fic_code* __restrict__ codes,
 }
 
 cudaError_t launch_order_mark(const void* codes, int64_t n_codes, int N, int B_max, int B_min,
-                              uint32_t* cellmap, uint32_t* cellflag, cudaStream_t s)
+                              uint32_t* cellmap, uint32_t* cellflag, cudaStream_t s,
+                              const uint32_t* n_dev)
 {
     if (n_codes == 0) return cudaSuccess;
     order_mark_kernel<<<(unsigned)((n_codes + 255) / 256), 256, 0, s>>>(
-        static_cast<const fic_code*>(codes), n_codes, N, B_max, B_min, cellmap, cellflag);
+        static_cast<const fic_code*>(codes), n_codes, n_dev, N, B_max, B_min, cellmap, cellflag);
     return cudaGetLastError();
 }
 

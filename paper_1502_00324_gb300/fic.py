@@ -94,7 +94,7 @@ assert CODE_DTYPE.itemsize == C.sizeof(FicCode) == 16
 EXPORTS = ["fic_encode", "fic_encode_ex", "fic_encode_batch", "fic_decode", "fic_domain_pool", "fic_result_free",
            "fic_strerror", "fic_stats_reset", "fic_stats_read", "fic_version",
            "fic_domain_pool_noalloc", "fic_last_error", "fic_pack", "fic_tune_mode",
-           "fic_tune_read", "fic_server_create", "fic_server_submit",
+           "fic_tune_read", "fic_graph_mode", "fic_graph_counts", "fic_server_create", "fic_server_submit",
            "fic_server_poll", "fic_server_stats_read", "fic_server_destroy"]
 
 
@@ -143,6 +143,8 @@ def lib():
                            C.POINTER(C.c_int64), C.POINTER(C.c_int64), vp]
     L.fic_tune_mode.argtypes = [C.c_int, C.POINTER(C.c_int)]
     L.fic_tune_read.argtypes = [C.POINTER(FicTuneEntry), C.c_int, C.POINTER(C.c_int)]
+    L.fic_graph_mode.argtypes = [C.c_int, C.POINTER(C.c_int)]
+    L.fic_graph_counts.argtypes = [C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     L.fic_server_create.argtypes = [C.POINTER(FicParams), C.POINTER(FicServerConfig),
                                     C.POINTER(vp)]
     L.fic_server_submit.argtypes = [vp, vp, C.c_int, C.POINTER(C.c_int64)]
@@ -354,6 +356,21 @@ def fic_tune_mode(mode=-1):
     prev = C.c_int(0)
     _check(lib().fic_tune_mode(int(mode), C.byref(prev)), "fic_tune_mode")
     return prev.value
+
+
+def fic_graph_mode(mode=-1):
+    """Set the graph mode (1: a configuration encoded before replays its
+    captured graph; 0: steps one by one); returns the previous mode."""
+    prev = C.c_int(0)
+    _check(lib().fic_graph_mode(int(mode), C.byref(prev)), "fic_graph_mode")
+    return prev.value
+
+
+def fic_graph_counts():
+    """(graphs captured, graph replays) of the synchronous entry points."""
+    cap, rep = C.c_int64(0), C.c_int64(0)
+    _check(lib().fic_graph_counts(C.byref(cap), C.byref(rep)), "fic_graph_counts")
+    return cap.value, rep.value
 
 
 def fic_tune_read():
