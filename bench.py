@@ -566,6 +566,66 @@ COMPARE_DESC = ("compare: the 512x512 precision image (1/f texture, alpha 2, see
                 "S = k/10, k = 1..10, at every step")
 
 
+def run_graph(args):
+    """Latency of one synchronous encode call, steps one by one (the host
+    reads the counts back between steps) against one captured graph of the
+    whole quadtree, over image sides; quadtree 16 -> 4, L = 2, entropy > 4.0
+    bits (the batching and serving configuration), device-resident images
+    and records, different images per call (the quadtrees differ)."""
+    import torch
+    import paper_1502_00324_gb300 as pkg
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    ss = [pkg.PAPER_S[b] for b in (16, 8, 4)]
+    rows = []
+    for n in (128, 256, 512, 1024):
+        imgs = [torch.from_numpy(fic_synth.one_over_f(n, 900 + i, 2.0)).to(dev) for i in range(8)]
+        out = torch.empty((n // 4) ** 2 * 16, dtype=torch.uint8, device=dev)
+        row = {"N": n}
+        for name, mode in (("eager", 0), ("graph", 1)):
+            pkg.fic_graph_mode(mode)
+
+            def enc(im):
+                return pkg.fic_encode_ex(im, n, 16, 4, 2, 4.0, ss, 8.0, stream=stream,
+                                         codes_out=out)
+            for _ in range(max(args.warmup, 3)):
+                for im in imgs[:2]:
+                    enc(im)
+            torch.cuda.synchronize()
+            cap0, rep0 = pkg.fic_graph_counts()
+            t0 = time.perf_counter()
+            reps = max(args.steps, 1)
+            codes = []
+            for _ in range(reps):
+                for im in imgs:
+                    r = enc(im)
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - t0) * 1e3 / (reps * len(imgs))
+            cap1, rep1 = pkg.fic_graph_counts()
+            for im in imgs[:3]:
+                r = enc(im)
+                codes.append(out[: r.n_codes * 16].cpu().numpy().tobytes())
+            row[name] = {"ms_per_encode": ms, "graph_replays": rep1 - rep0,
+                         "graph_captures": cap1 - cap0}
+            row[name + "_codes"] = codes
+        row["codes_identical"] = row.pop("eager_codes") == row.pop("graph_codes")
+        row["graph_speedup"] = row["eager"]["ms_per_encode"] / row["graph"]["ms_per_encode"]
+        rows.append(row)
+    pkg.fic_graph_mode(1)
+    line = {"metric": "ms per synchronous encode call, steps one by one vs one CUDA graph",
+            "workload": "graph", "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "dtype": "fp16->fp32 (exact int)",
+            "data": "synthetic",
+            "config": {"workload": "graph: 8 uint8 1/f images (alpha 2, seeds 900-907) per "
+                                   "side, quadtree 16->8->4, L=2, entropy > 4.0 bits, "
+                                   "S {0.1},{0.2,0.4},{0.3,0.8}, RMS tol 8; host wall time of "
+                                   "the synchronous call, device-resident input and records"},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_compare(args):
     """Encode time, quality and stored size of the proposed method
     (predefined S per step) against the entropy-based baseline (ten S values
@@ -633,7 +693,7 @@ def main():
     ap.add_argument("--legs", default="tensor,plain,e2e,cpu",
                     help="measurements to run (profiling runs use 'tensor' alone)")
     ap.add_argument("--workload", default="precision512",
-                    choices=["precision512", "batch64", "serving", "compare"],
+                    choices=["precision512", "batch64", "serving", "compare", "graph"],
                     help="precision512: the headline line; batch64: the 64-image batching "
                          "form; serving: the request server under a Poisson stream")
     ap.add_argument("--requests", type=int, default=200, help="serving: number of requests")
@@ -655,6 +715,8 @@ def main():
         return run_serving(args)
     if args.workload == "compare":
         return run_compare(args)
+    if args.workload == "graph":
+        return run_graph(args)
     return run_gpu(args)
 
 
