@@ -473,17 +473,28 @@ gather_kernel(const uint16_t* __restrict__ box, int N, int B, int L, int per,
               const uint32_t* __restrict__ dn_dev, StepParams sp, __half* __restrict__ D,
               float* __restrict__ cf, ColExact* __restrict__ ci)
 {
+    // Thread t: column c = block's first + 8 (t / (8 G)) + t % 8, k-group
+    // (t / 8) % G.  Eight consecutive threads write eight consecutive
+    // columns' 16-byte rows of one core matrix: 128 contiguous bytes.
     constexpr int G = K / 8;
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t c = gid / G;
-    const int kg = (int)(gid % G);
-    // columns used: the padded pool (cols_pad stays the layout's stride)
+    constexpr int kCols = 256 / G;  // columns per block (256 threads)
+    __shared__ int s_sum[kCols], s_sq[kCols];
+    const int t = threadIdx.x;
+    const int cl = t & 7, kg = (t >> 3) % G, cgp = t / (8 * G);
+    const int64_t c0 = (int64_t)blockIdx.x * kCols;
+    const int64_t c = c0 + cgp * 8 + cl;
+    if (t < kCols) {
+        s_sum[t] = 0;
+        s_sq[t] = 0;
+    }
+    // columns in use: the padded pool (cols_pad stays the layout's stride)
     int64_t cols = cols_pad;
     if (dn_dev) {
         dn = dev_count(dn, dn_dev);
         cols = min(cols_pad, round_up64(dn > 0 ? dn : 1, kColPad));
     }
-    if (c >= cols) return;  // cols * G is a multiple of 256: whole warps
+    __syncthreads();
+    if (c0 >= cols) return;  // whole block past the used columns (cols % kCols == 0)
     const bool real = c < dn;
     int x = 0, y = 0;
     if (real) {
@@ -497,7 +508,7 @@ gather_kernel(const uint16_t* __restrict__ box, int N, int B, int L, int per,
         }
     }
     const int n = B * B;
-    int s = 0, s2sum = 0;
+    int sum = 0, sq = 0;
     __align__(16) __half hv[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
@@ -506,35 +517,36 @@ gather_kernel(const uint16_t* __restrict__ box, int N, int B, int L, int per,
         if (real && k < n) {
             const int i = k / B, j = k % B;
             const int d = box[(int64_t)(y + 2 * i) * N + x + 2 * j];
-            s += d;
-            s2sum += d * d;
+            sum += d;
+            sq += d * d;
             val = d - kDomainCentre;
         }
         hv[e] = __int2half_rn(val);
     }
     *reinterpret_cast<uint4*>(D + tile_off(c, kg * 8, cols_pad, K)) =
         *reinterpret_cast<const uint4*>(hv);
-    int s2 = s2sum;
-#pragma unroll
-    for (int m = 1; m < G; m <<= 1) {
-        s += __shfl_xor_sync(0xffffffffu, s, m);
-        s2 += __shfl_xor_sync(0xffffffffu, s2, m);
-    }
-    if (kg != 0) return;
-    // constants in groups of 4 columns: constant j of column c at
-    // cf[((c / 4) * cw + j) * 4 + c % 4]
-    float* grp = cf + (c >> 2) * sp.cw * 4 + (c & 3);
     if (real) {
-        const long long vd = (long long)n * s2 - (long long)s * s;
-        grp[0] = (float)(s - kDomainCentre * n) * (1.0f / (float)n);
-        for (int t = 0; t < sp.ns; ++t)
-            grp[(1 + t) * 4] =
-                __double2float_rn((double)sp.p[t] * sp.p[t] * (double)vd / (double)n);
-        ci[c] = ColExact{s, s2};
+        atomicAdd(&s_sum[c - c0], sum);
+        atomicAdd(&s_sq[c - c0], sq);
+    }
+    __syncthreads();
+    if (t >= kCols) return;
+    // constants in groups of 4 columns: constant j of column cc at
+    // cf[((cc / 4) * cw + j) * 4 + cc % 4]
+    const int64_t cc = c0 + t;
+    float* grp = cf + (cc >> 2) * sp.cw * 4 + (cc & 3);
+    if (cc < dn) {
+        const int sd = s_sum[t], sd2 = s_sq[t];
+        const long long vd = (long long)n * sd2 - (long long)sd * sd;
+        grp[0] = (float)(sd - kDomainCentre * n) * (1.0f / (float)n);
+        for (int u = 0; u < sp.ns; ++u)
+            grp[(1 + u) * 4] =
+                __double2float_rn((double)sp.p[u] * sp.p[u] * (double)vd / (double)n);
+        ci[cc] = ColExact{sd, sd2};
     } else {
         grp[0] = 0.0f;
-        for (int t = 0; t < sp.ns; ++t) grp[(1 + t) * 4] = __int_as_float(0x7f800000);
-        ci[c] = ColExact{0, 0};
+        for (int u = 0; u < sp.ns; ++u) grp[(1 + u) * 4] = __int_as_float(0x7f800000);
+        ci[cc] = ColExact{0, 0};
     }
 }
 
@@ -587,8 +599,8 @@ cudaError_t launch_gather(const uint16_t* s2img, int N, int B, int L, int per,
                           unsigned long long* vd_max, unsigned long long* vd_min_key,
                           cudaStream_t s, const uint32_t* dn_dev)
 {
-    const int64_t threads = cols_pad * (K / 8);
-    const unsigned blocks = (unsigned)((threads + 255) / 256);
+    // 256 threads cover 256 / (K / 8) columns (8, 32 or 128), which divides kColPad
+    const unsigned blocks = (unsigned)(cols_pad / (256 / (K / 8)));
     switch (K) {
         case 16:
             gather_kernel<16><<<blocks, 256, 0, s>>>(s2img, N, B, L, per, pool_xy, dn, cols_pad,
