@@ -503,11 +503,13 @@ gather_kernel(const uint16_t* __restrict__ box, int N, int B, int L, int per,
             x = (int)(v & 0xffffu);
             y = (int)(v >> 16);
         } else {
-            x = (int)(c % per) * L;
-            y = (int)(c / per) * L;
+            const uint32_t cu = (uint32_t)c, pu = (uint32_t)per;  // c < 2^31
+            x = (int)(cu % pu) * L;
+            y = (int)(cu / pu) * L;
         }
     }
-    const int n = B * B;
+    const int n = B * B, lb = __ffs(B) - 1;  // B is a power of two
+    const uint16_t* __restrict__ base = box + (int64_t)y * N + x;
     int sum = 0, sq = 0;
     __align__(16) __half hv[8];
 #pragma unroll
@@ -515,8 +517,8 @@ gather_kernel(const uint16_t* __restrict__ box, int N, int B, int L, int per,
         const int k = kg * 8 + e;
         int val = 0;
         if (real && k < n) {
-            const int i = k / B, j = k % B;
-            const int d = box[(int64_t)(y + 2 * i) * N + x + 2 * j];
+            const int i = k >> lb, j = k & (B - 1);
+            const int d = base[2 * i * N + 2 * j];
             sum += d;
             sq += d * d;
             val = d - kDomainCentre;
