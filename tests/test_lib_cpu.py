@@ -77,3 +77,16 @@ def test_struct_layouts(fic):
     assert C.sizeof(f.FicSset) == 72
     # fic_result / fic_params are plain C layouts of int32/int64/double fields
     assert C.sizeof(f.FicParams) == 4 * 4 + 2 * 8 + 4 * 72 + 2 * 4
+
+
+def test_process_modes_set_and_read_on_host(fic):
+    # tuning and graph modes are process-wide settings: no device needed
+    prev = fic.fic_graph_mode(0)
+    assert prev in (0, 1)
+    assert fic.fic_graph_mode(prev) == 0
+    assert fic.fic_graph_mode() == prev
+    with pytest.raises(fic.FicError) as e:
+        fic.fic_graph_mode(2)
+    assert e.value.status == fic.fic.FIC_EINVAL
+    t = fic.fic_tune_mode(0)
+    assert fic.fic_tune_mode(t) == 0
