@@ -322,6 +322,16 @@ def run_gpu(args):
     tc = st_t["contract_tc"]
     achieved = tc["flops"] / (tc["ms"] / 1e3) / 1e12 if tc["ms"] > 0 else None
     kern_ms = {k: v["ms"] / args.steps for k, v in st_t.items() if isinstance(v, dict)}
+    # the memory-bound stages against the measured HBM copy bandwidth
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    stages = {}
+    for k in ("entropy", "scan", "gather", "range_prep", "split", "order"):
+        v = st_t.get(k)
+        if isinstance(v, dict) and v["ms"] > 0 and v["bytes"] > 0:
+            gbs = v["bytes"] / (v["ms"] / 1e3) / 1e9
+            stages[k] = {"ms_per_step": v["ms"] / args.steps,
+                         "bytes_per_step": v["bytes"] / args.steps,
+                         "GB/s": gbs, "frac_of_hbm": gbs / hbm}
     launches = sum(v["launches"] for k, v in st_t.items() if isinstance(v, dict))
 
     cpu = None
@@ -366,6 +376,9 @@ def run_gpu(args):
                      "algorithmic_flops_per_encode": tc["flops"] / max(args.steps, 1),
                      "peak_note": "of measured: bf16 dense burst (MEASURED_PEAKS.json); fp16 "
                                   "dense nominal equal"},
+        "stages_hbm": {"peak_gbs": hbm, "note": "algorithmic bytes / CUDA-event time of the "
+                       "stage's launches; peak = measured HBM copy bandwidth "
+                       "(MEASURED_PEAKS.json)", "stages": stages},
         "cpu_baseline": cpu,
         "e2e": {"value": (e2e_m / e2e_s / 1e9) if e2e_m else None, "unit": "Gmatch/s",
                 "h2d_bytes_per_step": int(N * N), "d2h_bytes_per_step": int(r_t.n_codes * 16)},

@@ -54,7 +54,8 @@ void Launcher::end(int launches, double flops, double bytes, int64_t matches)
 {
     if (rec_) {
         if (cur_.b) cudaEventRecordWithFlags(cur_.b, s_, cudaEventRecordExternal);
-        rec_->entries.push_back(GraphRec::Entry{kind_, launches, rec_->level, bytes, cur_.a, cur_.b});
+        rec_->entries.push_back(
+            GraphRec::Entry{kind_, launches, rec_->level, rec_->job, bytes, cur_.a, cur_.b});
         cur_.a = cur_.b = nullptr;
         return;
     }

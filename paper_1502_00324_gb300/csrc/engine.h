@@ -41,12 +41,13 @@ extern StatsState g_stats;
 // after every launch of the graph (graph.cu).
 struct GraphRec {
     struct Entry {
-        int kind, launches, level;
+        int kind, launches, level, job;
         double bytes;
         cudaEvent_t a, b;
     };
     bool timed = false;
     int level = -1;  // quadtree step being captured
+    int job = -1;    // image of the stage being captured (-1: all)
     std::vector<Entry> entries;
     ~GraphRec();
 };

@@ -425,10 +425,11 @@ int Engine::graph_build(GraphPlan& G, cudaStream_t /*s*/)
             const int N = G.Ns[(size_t)i];
             act[(size_t)i] = w.act0.as<uint32_t>();
             next[(size_t)i] = w.act1.as<uint32_t>();
+            G.rec.job = i;
             L.begin(FIC_K_GATHER);
             FIC_TRY(launch_init_ranges(act[(size_t)i], N / p.B_max, p.B_max, s));
             FIC_TRY(launch_box2(w.img.as<uint8_t>(), N, w.box2.as<uint16_t>(), s));
-            L.end(2);
+            L.end(2, 0.0, (double)N * N * 3.0);
         }
         for (int lvl = 0; lvl < nl; ++lvl) {
             G.rec.level = lvl;
@@ -437,12 +438,14 @@ int Engine::graph_build(GraphPlan& G, cudaStream_t /*s*/)
             const PlanJob* jobs = G.jobs[lvl].as<PlanJob>();
             if (use_list)
                 for (int i = 0; i < n; ++i) {
+                    G.rec.job = i;
                     int st = pool_launches(G.work[(size_t)i].get(), ds + i, entT_.as<long long>(),
                                            G.work[(size_t)i]->img.as<uint8_t>(), G.Ns[(size_t)i],
                                            h.B, p.L, top > 0 ? -1.0 : p.entropy_thresh, top,
                                            false, L, s);
                     if (st) return st;
                 }
+            G.rec.job = -1;
             L.begin(FIC_K_MISC);
             graph_level_begin_kernel<<<jb, 128, 0, s>>>(jobs, n, ds, lvl);
             FIC_TRY(cudaGetLastError());
@@ -457,6 +460,7 @@ int Engine::graph_build(GraphPlan& G, cudaStream_t /*s*/)
                 const int64_t cols = round_up(npos > 0 ? npos : 1, kColPad);
                 const int64_t R_max = (int64_t)(N / h.B) * (N / h.B);
                 const int64_t rows = 8 * round_up(R_max, 128);
+                G.rec.job = i;
                 FIC_TRY(cudaMemsetAsync(&ds[i].vd_max, 0, sizeof(unsigned long long), s));
                 FIC_TRY(cudaMemsetAsync(&ds[i].vd_min_key, 0xff, sizeof(unsigned long long), s));
                 L.begin(FIC_K_GATHER);
@@ -476,6 +480,7 @@ int Engine::graph_build(GraphPlan& G, cudaStream_t /*s*/)
                 // bound on the items: M tiles x chunks <= 16 SMs + M tiles
                 item_bound += 16LL * sms + rows / (h.iso ? 1024 : kMTile);
             }
+            G.rec.job = -1;
             PlanStep ps;
             ps.n_jobs = n;
             ps.iso = h.iso ? 1 : 0;
@@ -517,6 +522,7 @@ int Engine::graph_build(GraphPlan& G, cudaStream_t /*s*/)
                 const int64_t npos = G.positions[(size_t)i][(size_t)lvl];
                 const int64_t dn_max = top > 0 ? std::min<int64_t>(top, npos) : npos;
                 const int64_t R_max = (int64_t)(N / h.B) * (N / h.B);
+                G.rec.job = i;
                 StepCounts dc;
                 dc.R = &ds[i].R;
                 dc.dn = &ds[i].dn;
@@ -542,6 +548,7 @@ int Engine::graph_build(GraphPlan& G, cudaStream_t /*s*/)
                                              dc2));
                 L.end(2 + nlaunch, 0.0, (double)R_max * 64.0);
             }
+            G.rec.job = -1;
             L.begin(FIC_K_MISC);
             graph_level_end_kernel<<<jb, 128, 0, s>>>(jobs, n, ds, last ? 1 : 0);
             FIC_TRY(cudaGetLastError());
@@ -553,6 +560,7 @@ int Engine::graph_build(GraphPlan& G, cudaStream_t /*s*/)
             ImageWork& w = *G.work[(size_t)i];
             const int N = G.Ns[(size_t)i];
             const int64_t cells = (int64_t)(N / p.B_min) * (N / p.B_min);
+            G.rec.job = i;
             L.begin(FIC_K_ORDER);
             FIC_TRY(cudaMemsetAsync(w.cellflag.p, 0, sizeof(uint32_t) * cells, s));
             FIC_TRY(launch_order_mark(w.codes_tmp.p, cells, N, p.B_max, p.B_min,
@@ -643,7 +651,28 @@ int Engine::encode_graph(int n, const uint8_t* const* imgs, const int* Ns, const
         std::lock_guard<std::mutex> g(g_stats.mu);
         for (const GraphRec::Entry& e : G->rec.entries) {
             g_stats.st.launches[e.kind] += e.launches;
-            g_stats.st.bytes[e.kind] += e.bytes;
+            // stages whose work depends on the counts: the eager driver's
+            // algorithmic bytes from this call's counts
+            double bytes = e.bytes;
+            if (e.job >= 0) {
+                const Scalars& c = hs[e.job];
+                const int64_t cells = (int64_t)(Ns[e.job] / P.B_min) * (Ns[e.job] / P.B_min);
+                if (e.kind == FIC_K_ORDER) bytes = (double)cells * 16.0 + (double)c.n_codes * 32.0;
+                if (e.level >= 0) {
+                    const StepShape h = step_shape(P, e.level, G->choice[e.level]);
+                    const double R = c.lvl_R[e.level], dn = c.lvl_dn[e.level];
+                    const double cols = (double)round_up(dn > 0 ? (int64_t)dn : 1, kColPad);
+                    if (e.kind == FIC_K_GATHER)
+                        bytes = R > 0 ? cols * (2.0 * h.K + 4.0 * h.sp.cw + 8.0) + dn * 2.0 * h.n2
+                                      : 0.0;
+                    if (e.kind == FIC_K_RANGE_PREP)
+                        bytes = (double)rows_pad_for(h, (int64_t)R) * h.K * 2.0 + R * (h.n2 + 20.0);
+                    if (e.kind == FIC_K_SPLIT) bytes = R * 64.0;
+                    // an image already finished does no pool work (eager skips it)
+                    if ((e.kind == FIC_K_ENTROPY || e.kind == FIC_K_SCAN) && R == 0) bytes = 0.0;
+                }
+            }
+            g_stats.st.bytes[e.kind] += bytes;
             if ((e.kind == FIC_K_CONTRACT_TC || e.kind == FIC_K_CONTRACT_PLAIN) && e.level >= 0) {
                 const int B = P.B_max >> e.level;
                 for (int i = 0; i < n; ++i) {
