@@ -7,10 +7,12 @@
 //      of all slots stay within the budget (slots keep their buffers between
 //      images; idle slots are emptied when room is needed);
 //   2. begin() for the images admitted now (upload, 2x2 sums, top ranges);
-//   3. one Engine::step() over every admitted image: each advances one
-//      quadtree step, with one grouped contraction launch per step present;
-//   4. finished images: records ordered and copied to the host, the slot
-//      freed, pollers woken.
+//   3. Engine::step() over the admitted images of side <= 512, then over
+//      the larger ones: each image advances one quadtree step, with one
+//      grouped contraction launch per step present in the class;
+//   4. after each class, its finished images: records ordered and copied to
+//      the host, the slot freed, pollers woken (a small image does not wait
+//      for the large images' step of the same iteration).
 // Images are independent: the engine gives each the same records it would
 // get alone (its own pool, its own partial bests, its own split decisions).
 #include <chrono>
@@ -30,6 +32,10 @@
 using namespace fic;
 
 namespace {
+
+// Side classes of an iteration: images up to this side step (and finish)
+// before the larger ones.
+constexpr int kSmallSide = 512;
 
 struct Request {
     int64_t ticket = 0;
@@ -220,43 +226,41 @@ struct fic_server {
             }
             if (inflight.empty()) continue;
 
-            // 3. one quadtree step of every image in flight
-            std::vector<Job*> jobs;
-            bool levels[FIC_MAX_LEVELS] = {false, false, false, false};
-            for (auto& f : inflight) {
-                jobs.push_back(&f->job);
-                f->steps += 1;
-                if (inflight.size() > 1) f->shared += 1;
-                if (f->job.lvl < FIC_MAX_LEVELS) levels[f->job.lvl] = true;
-            }
-            int status = eng.step(p, jobs, L, stream);
-            if (status) {
-                fail_all_inflight(status);
-                continue;
-            }
-
-            // 4. finished images: records to the host
-            bool any_done = false;
-            std::vector<int> finishing;
-            for (size_t i = 0; i < inflight.size(); ++i)
-                if (inflight[i]->job.done) {
-                    any_done = true;
-                    finishing.push_back((int)i);
-                    status = eng.finish(inflight[i]->job, p, nullptr, 0, L, stream);
-                    if (status) break;
+            // 3-4. one quadtree step of every image in flight, smaller images
+            // first: each side class steps in its own grouped launches and
+            // its finished images are released before the next class steps,
+            // so a small image does not wait for a large image's step
+            const double n_start = (double)inflight.size();
+            bool failed = false;
+            for (int cls = 0; cls < 2 && !failed; ++cls) {
+                std::vector<Job*> jobs;
+                bool levels[FIC_MAX_LEVELS] = {false, false, false, false};
+                for (auto& f : inflight)
+                    if ((f->req.N > kSmallSide) == (cls == 1)) jobs.push_back(&f->job);
+                if (jobs.empty()) continue;
+                for (auto& f : inflight)
+                    if ((f->req.N > kSmallSide) == (cls == 1)) {
+                        f->steps += 1;
+                        if (jobs.size() > 1) f->shared += 1;
+                        if (f->job.lvl < FIC_MAX_LEVELS) levels[f->job.lvl] = true;
+                    }
+                int status = eng.step(p, jobs, L, stream);
+                bool any_done = false;
+                if (!status)
+                    for (Job* j : jobs)
+                        if (j->done) {
+                            any_done = true;
+                            status = eng.finish(*j, p, nullptr, 0, L, stream);
+                            if (status) break;
+                        }
+                if (!status && any_done) status = to_status(cudaStreamSynchronize(stream));
+                if (status) {
+                    fail_all_inflight(status);
+                    failed = true;
+                    break;
                 }
-            if (!status && any_done) status = to_status(cudaStreamSynchronize(stream));
-            if (status) {
-                fail_all_inflight(status);
-                continue;
-            }
-            {
                 std::lock_guard<std::mutex> g(mu);
-                st.iterations += 1;
                 for (bool b : levels) st.contraction_launches += b ? 1 : 0;
-                inflight_sum += (double)inflight.size();
-                st.mean_inflight = inflight_sum / (double)st.iterations;
-                st.busy_ms += now_ms() - t_iter;
                 std::vector<std::unique_ptr<InFlight>> keep;
                 for (auto& f : inflight) {
                     if (f->job.done)
@@ -267,6 +271,14 @@ struct fic_server {
                 inflight.swap(keep);
                 st.inflight = (int64_t)inflight.size();
                 if (any_done) cv_done.notify_all();
+            }
+            if (failed) continue;
+            {
+                std::lock_guard<std::mutex> g(mu);
+                st.iterations += 1;
+                inflight_sum += n_start;
+                st.mean_inflight = inflight_sum / (double)st.iterations;
+                st.busy_ms += now_ms() - t_iter;
             }
         }
     }
