@@ -69,13 +69,14 @@ __device__ __forceinline__ float iso_max(const float (&x)[P][W], int i)
     else return fmaxf(x[0][i], x[1][i]);
 }
 
-// Filter pass over 16 columns (4 groups of 4) x P isometries of one range.
+// Filter pass over W columns (W / 4 groups of 4) x P isometries of one
+// range: the minimum of each group (gm, for pass 2) and of the block.
 template <int NS, int P, int W>
 __device__ __forceinline__ float iso_pass1(const float (&x)[P][W], const float* __restrict__ cf,
-                                           int g0, float na, const StepParams& sp)
+                                           int g0, float na, const StepParams& sp,
+                                           float (&gm)[W / 4])
 {
     constexpr int cw = 1 + NS;
-    float mn0 = __int_as_float(0x7f800000), mn1 = mn0;
     const uint64_t nak = pk2(na, na);
     uint64_t nk[NS];
 #pragma unroll
@@ -89,17 +90,22 @@ __device__ __forceinline__ float iso_pass1(const float (&x)[P][W], const float* 
         const float4 m = cg[0];
         const uint64_t t01 = fma2(nak, pk2(m.x, m.y), pk2(c[0], c[1]));
         const uint64_t t23 = fma2(nak, pk2(m.z, m.w), pk2(c[2], c[3]));
+        float g01 = __int_as_float(0x7f800000), g23 = g01;
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             const float4 b = cg[1 + s];
             float f0, f1, f2, f3;
             upk2(fma2(nk[s], t01, pk2(b.x, b.y)), f0, f1);
             upk2(fma2(nk[s], t23, pk2(b.z, b.w)), f2, f3);
-            mn0 = fmin3(mn0, f0, f1);
-            mn1 = fmin3(mn1, f2, f3);
+            g01 = fmin3(g01, f0, f1);
+            g23 = fmin3(g23, f2, f3);
         }
+        gm[g] = fminf(g01, g23);
     }
-    return fminf(mn0, mn1);
+    float mn = gm[0];
+#pragma unroll
+    for (int g = 1; g < W / 4; ++g) mn = fminf(mn, gm[g]);
+    return mn;
 }
 
 // Exact re-scoring of the candidates of a 16-column block whose filter is
@@ -109,6 +115,7 @@ __device__ __forceinline__ float iso_pass1(const float (&x)[P][W], const float* 
 // the best) or h > h* - 1 (index above it).
 template <int NS, int P, int W>
 __device__ __forceinline__ void iso_pass2(RowState& st, const float (&x)[P][W], float mn,
+                                          const float (&gm)[W / 4],
                                           const float* __restrict__ cf, int g0, int col_base,
                                           int iso_base, float na, float delta, float inv_n,
                                           int sr, const ColExact* __restrict__ ci, int dn,
@@ -119,6 +126,7 @@ __device__ __forceinline__ void iso_pass2(RowState& st, const float (&x)[P][W], 
     float te = fminf(st.thr, __fadd_ru(mn, 2.0f * delta));
 #pragma unroll
     for (int g = 0; g < W / 4; ++g) {
+        if (!(gm[g] <= te)) continue;  // no column of this group can pass
         const float* cg = cf + (size_t)(g0 + g) * cw * 4;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -429,9 +437,10 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
                         }
                         if (valid) {
                             const int g0 = (hsel * kWarpCols + kChunk * ch) / 4;
-                            const float mn = iso_pass1<NS, kPass, kChunk>(x, cfs, g0, -r.a, sp);
+                            float gm[kChunk / 4];
+                            const float mn = iso_pass1<NS, kPass, kChunk>(x, cfs, g0, -r.a, sp, gm);
                             if (mn <= st.thr)
-                                iso_pass2<NS, kPass, kChunk>(st, x, mn, cfs, g0, ct * kN,
+                                iso_pass2<NS, kPass, kChunk>(st, x, mn, gm, cfs, g0, ct * kN,
                                                              pass * kPass, -r.a, r.delta, inv_n,
                                                              r.sr, qci, qdn, &sp);
                         }
