@@ -109,7 +109,9 @@ __device__ __forceinline__ float iso_pass1(const float (&x)[P][W], const float* 
 }
 
 // Exact re-scoring of the candidates of a 16-column block whose filter is
-// within 2 delta of the block minimum mn and under the range's threshold.
+// within 2 delta of the block minimum mn and under the range's threshold
+// (ci: the tile's exact column sums, staged in shared memory with its
+// filter constants, indexed by the column within the tile).
 // Candidates of one range arrive out of index order across passes, so a
 // candidate is skipped only when its lower bound proves h > h* (index below
 // the best) or h > h* - 1 (index above it).
@@ -156,7 +158,8 @@ __device__ __forceinline__ void iso_pass2(RowState& st, const float (&x)[P][W], 
                         pack_idx((unsigned)col, iso, 0) > st.idx ? st.h - 1 : st.h;
                     if (lo > __ll2float_ru(bound) * inv_n) continue;
                 }
-                st = exact_col(st, xj, cg, e, col, iso, na, delta, inv_n, sr, ci, dn, spp, te);
+                st = exact_col(st, xj, cg, e, col, iso, na, delta, inv_n, sr,
+                               ci + (g0 + g) * 4 + e, dn, spp, te);
                 te = fminf(te, st.thr);
             }
         }
@@ -208,7 +211,9 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
     constexpr uint32_t kBStageBytes = (uint32_t)kN * K * 2u;
     constexpr uint32_t kSbo = K * 16u;                // 8-row group stride
     constexpr uint32_t kIdesc = idesc_f16_f32(128, kN);
-    const uint32_t cf_bytes = (uint32_t)kN * (uint32_t)sp.cw * 4u;
+    // constants ring: per tile the filter constants, then the exact column sums
+    const uint32_t cfc_bytes = (uint32_t)kN * (uint32_t)sp.cw * 4u;
+    const uint32_t cf_bytes = cfc_bytes + (uint32_t)kN * (uint32_t)sizeof(ColExact);
     const int nstage = P.nstage, ncf = P.ncf;
 
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -292,7 +297,9 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
                 if (elect_one()) {
                     mbar_expect_tx(cff(cidx), cf_bytes);
                     bulk_g2s(smem_u32(sCF + (size_t)cidx * cf_bytes), Q.cf + (int64_t)ct * kN * sp.cw,
-                             cf_bytes, cff(cidx));
+                             cfc_bytes, cff(cidx));
+                    bulk_g2s(smem_u32(sCF + (size_t)cidx * cf_bytes + cfc_bytes),
+                             Q.ci + (int64_t)ct * kN, cf_bytes - cfc_bytes, cff(cidx));
                 }
                 __syncwarp();
                 ++cfi;
@@ -400,7 +407,6 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
             item_coords(Q, local, chunk, mtile);
             const int ct0 = chunk * Q.per_chunk;
             const int ct1 = min(Q.n_ct, ct0 + Q.per_chunk);
-            const ColExact* qci = Q.ci;
             const int qdn = Q.dn;
             const int range = mtile * 128 + quad * 32 + lane;
             const RowConst r = range < Q.R ? Q.rc[range] : RowConst{0, 0, 0.f, 0.f};
@@ -418,6 +424,8 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
                 if (valid) gseen = __ldcg(Q.gbest + range);
                 if (!(ok = mbar_wait(cff(cidx), cphase, err, kWaitCycles))) break;
                 const float* cfs = reinterpret_cast<const float*>(sCF + (size_t)cidx * cf_bytes);
+                const ColExact* cis =
+                    reinterpret_cast<const ColExact*>(sCF + (size_t)cidx * cf_bytes + cfc_bytes);
 #pragma unroll 1
                 for (int pass = 0; pass < kPasses; ++pass) {
                     if (!(ok = mbar_wait(tfull(slot), tphase, err, kWaitCycles))) break;
@@ -442,7 +450,7 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
                             if (mn <= st.thr)
                                 iso_pass2<NS, kPass, kChunk>(st, x, mn, gm, cfs, g0, ct * kN,
                                                              pass * kPass, -r.a, r.delta, inv_n,
-                                                             r.sr, qci, qdn, &sp);
+                                                             r.sr, cis, qdn, &sp);
                         }
                     }
                     if (++slot == kSlots) {
@@ -495,7 +503,7 @@ size_t iso_layout(int cw, int* nstage_out, int* ncf_out)
     constexpr int kN = IsoShape<K>::N;
     const size_t a_bytes = (size_t)8 * 128 * K * 2;
     const size_t stage = (size_t)kN * K * 2;
-    const size_t cf_tile = (size_t)kN * cw * 4;
+    const size_t cf_tile = (size_t)kN * cw * 4 + (size_t)kN * sizeof(ColExact);
     const int ncf = 16;
     const size_t fixed = a_bytes + (size_t)ncf * cf_tile + 1024;
     int ns = (int)((kSmemBudget - fixed) / stage);

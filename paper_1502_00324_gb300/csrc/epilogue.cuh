@@ -75,12 +75,12 @@ __device__ __forceinline__ float col_filter(const float* __restrict__ cg, int e,
 // arrays statically indexed.
 static __device__ __noinline__ RowState exact_col(RowState st, float x, const float* __restrict__ cg,
                                            int e, int col, unsigned iso, float na, float delta,
-                                           float inv_n, int sr, const ColExact* __restrict__ ci,
+                                           float inv_n, int sr, const ColExact* __restrict__ cep,
                                            int dn, const StepParams* __restrict__ spp, float te)
 {
     const StepParams& sp = *spp;
     if (col >= dn) return st;
-    const ColExact ce = ci[col];
+    const ColExact ce = *cep;  // this column's sums
     const int cprime = __float2int_rn(x);
     for (int s = 0; s < sp.ns; ++s) {
         const float f = col_filter(cg, e, na, x, sp, s);
@@ -207,8 +207,8 @@ __device__ __forceinline__ void epi_pass2(RowState& st, const float (&x)[4 * NG]
                     }
                     if (lo > __ll2float_ru(st.h - 1) * inv_n) continue;
                 }
-                st = exact_col(st, x[4 * g + e], cg, e, col0 + e, iso, na, delta, inv_n, sr, ci,
-                               dn, spp, te);
+                st = exact_col(st, x[4 * g + e], cg, e, col0 + e, iso, na, delta, inv_n, sr,
+                               ci + col0 + e, dn, spp, te);
                 te = fminf(te, st.thr);
             }
         }
