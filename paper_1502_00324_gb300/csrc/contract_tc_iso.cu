@@ -123,25 +123,41 @@ __device__ __forceinline__ void iso_pass2(RowState& st, const float (&x)[P][W], 
                                           int sr, const ColExact* __restrict__ ci, int dn,
                                           const StepParams* __restrict__ spp)
 {
+    // Compact code on purpose: this path is rare, and fully unrolled it
+    // would be thousands of instructions that miss the instruction cache on
+    // every entry while the other warps of the CTA wait for this one's TMEM
+    // slot.  The chunk goes to a local copy, indexed in rolled loops.
     const StepParams& sp = *spp;
     constexpr int cw = 1 + NS;
     float te = fminf(st.thr, __fadd_ru(mn, 2.0f * delta));
+    unsigned gmask = 0;
 #pragma unroll
-    for (int g = 0; g < W / 4; ++g) {
-        if (!(gm[g] <= te)) continue;  // no column of this group can pass
+    for (int g = 0; g < W / 4; ++g) gmask |= (gm[g] <= te) ? (1u << g) : 0u;
+    if (!gmask) return;
+    float xl[P * W];
+#pragma unroll
+    for (int j = 0; j < P; ++j)
+#pragma unroll
+        for (int c = 0; c < W; ++c) xl[j * W + c] = x[j][c];
+#pragma unroll 1
+    for (; gmask; gmask &= gmask - 1) {
+        const int g = __ffs(gmask) - 1;
         const float* cg = cf + (size_t)(g0 + g) * cw * 4;
-#pragma unroll
+#pragma unroll 1
         for (int e = 0; e < 4; ++e) {
-            const float cmax = iso_max<P, W>(x, 4 * g + e);
+            const int c = 4 * g + e;
+            float cmax = xl[c];
+#pragma unroll
+            for (int j = 1; j < P; ++j) cmax = fmaxf(cmax, xl[j * W + c]);
             float fm = __int_as_float(0x7f800000);
 #pragma unroll
             for (int s = 0; s < NS; ++s) fm = fminf(fm, col_filter(cg, e, na, cmax, sp, s));
             if (!(fm <= te)) continue;
             const int col = (g0 + g) * 4 + e + col_base;
-#pragma unroll
+#pragma unroll 1
             for (int j = 0; j < P; ++j) {
                 const unsigned iso = (unsigned)(iso_base + j);
-                const float xj = x[j][4 * g + e];
+                const float xj = xl[j * W + c];
                 float fj = __int_as_float(0x7f800000), lo = fj;
 #pragma unroll
                 for (int s = 0; s < NS; ++s) {
