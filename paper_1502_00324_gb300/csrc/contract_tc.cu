@@ -43,9 +43,6 @@ using namespace tc;
 #ifndef FIC_TC_NTILE
 #define FIC_TC_NTILE 256
 #endif
-#ifndef FIC_TC_PIPE
-#define FIC_TC_PIPE 0
-#endif
 constexpr int kEpiWarps = FIC_TC_EPI_WARPS;     // epilogue warps, a multiple of 4
 constexpr int kN = FIC_TC_NTILE;                // MMA N = pool columns per tile
 constexpr int kThreads = 32 * (2 + kEpiWarps);
@@ -300,40 +297,6 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
                 const float* cfs = reinterpret_cast<const float*>(sCF + (size_t)cb * cf_bytes);
                 const uint32_t tb = tmem_base + ((uint32_t)(quad * 32) << 16) +
                                     (uint32_t)(acc * 256 + cq * kColsPerEpiWarp);  // 256-column slots
-#if FIC_TC_PIPE
-                // double-buffered 32-column loads: block b+1 streams in while
-                // pass 1 scores block b; the wait comes before the (rare) pass 2
-                // so no register of an unfinished load is live across its calls
-                float xa[32], xb[32];
-                __syncwarp();
-                tmem_ld32_issue(tb, xa);
-                tmem_wait32(xa);
-#pragma unroll
-                for (int b = 0; b < kEpiBlocks; ++b) {
-                    float(&cur)[32] = (b & 1) ? xb : xa;
-                    float(&nxt)[32] = (b & 1) ? xa : xb;
-                    const bool more = b + 1 < kEpiBlocks;
-                    if (more) {
-                        __syncwarp();
-                        tmem_ld32_issue(tb + 32u * (b + 1), nxt);
-                    } else {
-                        // the accumulator is in registers: hand TMEM back to the MMA
-                        tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(tempty(acc));
-                    }
-                    const int g0 = (cq * kColsPerEpiWarp + 32 * b) / 4;
-                    const float mn = valid ? epi_pass1<NS, 8>(cur, cfs, g0, 1, -r.a, &sp)
-                                           : __int_as_float(0x7f800000);
-                    if (more) {
-                        __syncwarp();
-                        tmem_wait32(nxt);
-                    }
-                    if (mn <= st.thr)
-                        epi_pass2<NS, 8>(st, cur, mn, cfs, g0, 1, ct * kN, iso, -r.a, r.delta,
-                                         inv_n, r.sr, qci, qdn, &sp);
-                }
-#else
 #pragma unroll 1
                 for (int b = 0; b < kEpiBlocks; ++b) {
                     float x[32];
@@ -351,7 +314,6 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
                                           ct * kN, iso, -r.a, r.delta, inv_n, r.sr, qci, qdn,
                                           &sp);
                 }
-#endif
                 if (st.h < gpub) {
                     atomicMin(gb, st.h);
                     gpub = st.h;
