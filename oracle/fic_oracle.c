@@ -24,7 +24,7 @@
  *   Sec. 3.3  stored record: step, range mean, isometry, domain address, S.
  *   Eq. 4     PSNR.
  *
- * Readings of points the paper leaves open (each also listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - decimation is the 2x2 average, carried as the integer 2x2 SUM d' so
  *     that d = d'/4 and all arithmetic stays integral;
  *   - S = p/q with one common denominator q per step;
