@@ -21,6 +21,7 @@ oracle on a bounded sample of the same workload instead.
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
 import statistics
@@ -80,32 +81,52 @@ def measured_traffic():
 
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    """nvidia-smi samples of SM clock and throttle reasons.  Each sample carries
+    nvidia-smi's own timestamp, so only the samples taken between begin() and
+    end() (the timed steps) are reported; when none fell inside (a region
+    shorter than the sampling period), the samples of the whole run are, and
+    'window' says so."""
 
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
-    def __init__(self, index):
+    def __init__(self, index, period_ms=50):
         self.index = index
+        self.period_ms = period_ms
         self.proc = None
         self.lines = []
         self.t = None
+        self.region = [None, None]
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception:
             self.proc = None
 
+    def begin(self):
+        self.region[0] = datetime.datetime.now()
+
+    def end(self):
+        self.region[1] = datetime.datetime.now()
+
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+
+    @staticmethod
+    def _when(text):
+        try:
+            return datetime.datetime.strptime(text, "%Y/%m/%d %H:%M:%S.%f")
+        except ValueError:
+            return None
 
     def stop(self):
         if self.proc is None:
@@ -115,22 +136,29 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, smax, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        if self.t is not None:
+            self.t.join(timeout=5)
+        rows = []
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax = float(parts[2])
+                sm, smax = float(parts[2]), float(parts[3])
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+            act = {nm for nm, v in zip(self.REASONS, parts[6:10]) if v.lower().startswith("active")}
+            rows.append((self._when(parts[0]), sm, smax, act))
+        t0, t1 = self.region
+        inside = [r for r in rows
+                  if t0 is not None and t1 is not None and r[0] is not None and t0 <= r[0] <= t1]
+        use = inside if inside else rows
+        return {"sm_mhz": statistics.median([r[1] for r in use]) if use else None,
+                "sm_max_mhz": use[-1][2] if use else None,
+                "reasons": sorted(set().union(*[r[3] for r in use])) if use else [],
+                "samples": len(use),
+                "window": "timed steps" if inside else "whole run (no sample inside the timed steps)",
+                "period_ms": self.period_ms}
 
 
 # ---------------------------------------------------------------- CPU oracle timing
@@ -240,7 +268,7 @@ def run_gpu(args):
             import torch.distributed as dist
             dist.barrier()
 
-    def timed(engine, steps, warmup, timing):
+    def timed(engine, steps, warmup, timing, sampler=None):
         for _ in range(warmup):
             enc(engine)
         torch.cuda.synchronize()
@@ -248,6 +276,8 @@ def run_gpu(args):
         evs = []
         barrier()
         torch.cuda.synchronize()
+        if sampler is not None:
+            sampler.begin()
         t_wall = time.perf_counter()
         matches = 0
         for _ in range(steps):
@@ -260,6 +290,8 @@ def run_gpu(args):
             evs.append((e0, e1))
             matches += r.total_matches
         torch.cuda.synchronize()
+        if sampler is not None:
+            sampler.end()
         barrier()
         wall = time.perf_counter() - t_wall
         ms = sum(a.elapsed_time(b) for a, b in evs)
@@ -269,7 +301,7 @@ def run_gpu(args):
     # tensor-core engine (the headline), clocks sampled during the timed steps
     sampler = ClockSampler(dev.index)
     sampler.start()
-    ms_t, m_t, st_t, r_t, wall_t = timed(pkg.ENGINE_TENSOR, args.steps, args.warmup, True)
+    ms_t, m_t, st_t, r_t, wall_t = timed(pkg.ENGINE_TENSOR, args.steps, args.warmup, True, sampler)
     clocks = sampler.stop()
     codes_t = dcodes[: r_t.n_codes * 16].cpu().numpy().copy()
 
@@ -424,12 +456,14 @@ def run_batch(args):
     def one_by_one():
         return [pkg.fic_encode_ex(d, d.shape[0], *args_enc, stream=stream) for d in dimgs]
 
-    def timed(fn, steps, warmup, timing=False):
+    def timed(fn, steps, warmup, timing=False, sampler=None):
         for _ in range(warmup):
             fn()
         torch.cuda.synchronize()
         pkg.fic_stats_reset(timing=timing)
         ms, out = [], None
+        if sampler is not None:
+            sampler.begin()
         for _ in range(steps):
             flush.fill_(1)
             e0 = torch.cuda.Event(enable_timing=True)
@@ -439,11 +473,13 @@ def run_batch(args):
             e1.record(stream)
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
+        if sampler is not None:
+            sampler.end()
         return ms, out, pkg.fic_stats_read()
 
     sampler = ClockSampler(dev.index)
     sampler.start()
-    ms_b, out_b, st_b = timed(batch, args.steps, args.warmup, True)
+    ms_b, out_b, st_b = timed(batch, args.steps, args.warmup, True, sampler)
     clocks = sampler.stop()
     ms_s, out_s, _ = timed(one_by_one, max(1, min(args.steps, 3)), 1)
     identical = all(np.array_equal(a.codes, b.codes) for a, b in zip(out_b, out_s))
@@ -519,6 +555,7 @@ def run_serving(args):
     tickets = [None] * len(imgs)
     sampler = ClockSampler(dev.index)
     sampler.start()
+    sampler.begin()
     t0 = time.perf_counter()
 
     def feed():
@@ -537,6 +574,7 @@ def run_serving(args):
         results.append(srv.poll(tickets[i], wait_ms=-1))
     th.join()
     wall = time.perf_counter() - t0
+    sampler.end()
     clocks = sampler.stop()
     st = srv.stats()
     srv.close()
@@ -700,7 +738,7 @@ def run_compare(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--legs", default="tensor,plain,e2e,cpu",

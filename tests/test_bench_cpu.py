@@ -1,0 +1,84 @@
+"""Host checks of bench.py's clock record: samples are filtered by
+nvidia-smi's own timestamp to the timed region, throttle reasons are read
+per sample, and a region too short for any sample falls back to the whole
+run and says so.  A fake nvidia-smi on PATH stands in for the real one."""
+from __future__ import annotations
+
+import os
+import stat
+import sys
+import time
+
+import pytest
+
+import bench
+
+FAKE = r'''#!{py}
+import datetime, os, sys, time
+until = float(os.environ["FAKE_CAP_UNTIL"])  # power cap active before this time
+while True:
+    now = datetime.datetime.now()
+    cap = "Active" if time.time() < until else "Not Active"
+    sm = 1500 if cap == "Active" else 2070
+    print(now.strftime("%Y/%m/%d %H:%M:%S.%f")[:-3] + ", 0, %d, 2070, 612.5, 0x0, Not Active, "
+          "Not Active, Not Active, %s" % (sm, cap), flush=True)
+    time.sleep(0.01)
+'''
+
+
+@pytest.fixture
+def fake_smi(tmp_path, monkeypatch):
+    exe = tmp_path / "nvidia-smi"
+    exe.write_text(FAKE.replace("{py}", sys.executable))
+    exe.chmod(exe.stat().st_mode | stat.S_IXUSR)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ.get("PATH", ""))
+    return exe
+
+
+def test_samples_inside_the_timed_region_only(fake_smi, monkeypatch):
+    cap_until = time.time() + 0.1
+    monkeypatch.setenv("FAKE_CAP_UNTIL", str(cap_until))
+    s = bench.ClockSampler(0, period_ms=10)
+    s.start()
+    time.sleep(max(0.0, cap_until - time.time()) + 0.05)  # the power-capped samples
+    s.begin()
+    time.sleep(0.3)
+    s.end()
+    time.sleep(0.1)
+    c = s.stop()
+    assert c["window"] == "timed steps"
+    assert c["samples"] >= 5
+    assert c["sm_mhz"] == 2070.0 and c["sm_max_mhz"] == 2070.0
+    assert c["reasons"] == []
+
+
+def test_reasons_seen_in_the_region_are_reported(fake_smi, monkeypatch):
+    monkeypatch.setenv("FAKE_CAP_UNTIL", str(time.time() + 100.0))
+    s = bench.ClockSampler(0, period_ms=10)
+    s.begin()              # every sample of the region is power-capped
+    s.start()
+    time.sleep(0.4)
+    s.end()
+    c = s.stop()
+    assert c["window"] == "timed steps"
+    assert "sw_power_cap" in c["reasons"]
+
+
+def test_short_region_falls_back_to_the_whole_run(fake_smi, monkeypatch):
+    monkeypatch.setenv("FAKE_CAP_UNTIL", "0")
+    s = bench.ClockSampler(0, period_ms=10)
+    s.start()
+    time.sleep(0.3)
+    t = bench.datetime.datetime.now()
+    s.region = [t, t - bench.datetime.timedelta(seconds=1)]  # empty region
+    c = s.stop()
+    assert c["window"].startswith("whole run")
+    assert c["samples"] >= 3
+
+
+def test_missing_nvidia_smi(tmp_path, monkeypatch):
+    monkeypatch.setenv("PATH", str(tmp_path))
+    s = bench.ClockSampler(0)
+    s.start()
+    c = s.stop()
+    assert c["sm_mhz"] is None and c["reasons"] == ["nvidia-smi unavailable"]
