@@ -51,9 +51,12 @@ _lib = None
 
 
 def lib():
+    """The compiled oracle.  FIC_ORACLE_LIB names another build of the same
+    source to load instead: the pins' mutation test runs them against copies
+    of the oracle with a planted mistake."""
     global _lib
     if _lib is None:
-        path = _build()
+        path = os.environ.get("FIC_ORACLE_LIB") or _build()
         L = C.CDLL(path)
         u8p = C.POINTER(C.c_uint8)
         i32p = C.POINTER(C.c_int32)

@@ -6,6 +6,7 @@ with oracle/fic_oracle.c, so a mistake in one is not repeated in the other.
 """
 from __future__ import annotations
 
+import math
 from fractions import Fraction
 
 import numpy as np
@@ -142,7 +143,7 @@ def brute_encode(img: np.ndarray, B_max: int, B_min: int, L: int, thr: float, ss
         sides.append(b)
         b //= 2
     pools = [pool_fn(s) if pool_fn else brute_pool(img, s, L, thr) for s in sides]
-    tol_f = Fraction(round(16 * tol), 16)
+    tol_f = Fraction(math.floor(16 * tol + 0.5), 16)  # e16 / 16, halves up
     out = []
 
     def rec(x, y, lvl):

@@ -369,6 +369,27 @@ def test_split_threshold_is_rms_greater_than_tol():
             assert (len(top) == 0) == split
 
 
+def test_split_tolerance_is_quantised_to_sixteenths():
+    """tol enters the split test as e16 / 16 with e16 = round(16 tol), halves
+    up.  For a range whose RMS error e lies in [k/16, (k+1)/16): tol just
+    above k/16 + 1/32 (or exactly there) rounds up to (k+1)/16 > e, so the
+    range is kept; tol at k/16 + 1/64 rounds to k/16, so it splits unless
+    e = k/16 exactly.  Errors from an exhaustive search (tests/brute.py)."""
+    img = fic_synth.one_over_f(32, 4)
+    ss = [(10, [2, 4]), (10, [3, 8])]
+    pool = brute.brute_pool(img, 8, 2, -1.0)
+    for tx, ty in [(0, 0), (8, 0), (16, 8), (24, 24)]:
+        score, *_ = brute.brute_search(img, tx, ty, 8, pool, ss[0])
+        ms = Fraction(score, 16 * 100 * 64) / 64       # E / n = RMS^2
+        k = math.isqrt(math.floor(256 * ms))            # k/16 <= RMS < (k+1)/16
+        assert Fraction(k * k, 256) <= ms < Fraction((k + 1) ** 2, 256)
+        for frac, keep in [(0.75, True), (0.5, True), (0.25, ms == Fraction(k * k, 256))]:
+            tol = (k + frac) / 16
+            codes, _ = oracle.encode(img, 8, 4, 2, -1.0, ss, tol)
+            top = [c for c in codes if c["rx"] == tx and c["ry"] == ty and c["level"] == 0]
+            assert (len(top) == 1) == keep, (tx, ty, k, frac)
+
+
 # ---------------------------------------------------------------- decoder, eq. 4
 
 def test_decoder_one_iteration_matches_literal():
