@@ -80,6 +80,36 @@ def measured_traffic():
 
 
 # ---------------------------------------------------------------- clocks
+def smi_device_id(dev):
+    """The nvidia-smi --id of torch device `dev`.  torch numbers the devices
+    CUDA_VISIBLE_DEVICES leaves visible from 0, nvidia-smi numbers every GPU of
+    the machine, so torch's index can name another process's GPU.  Candidates,
+    first accepted by nvidia-smi wins: the device's UUID, its entry in
+    CUDA_VISIBLE_DEVICES, torch's index."""
+    import torch
+    cands = []
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid).strip()
+        if u:
+            cands.append(u if u.startswith(("GPU-", "MIG-")) else "GPU-" + u)
+    except Exception:
+        pass
+    vis = [v.strip() for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    if dev.index is not None and dev.index < len(vis):
+        cands.append(vis[dev.index])
+    cands.append(str(dev.index or 0))
+    for c in cands:
+        try:
+            out = subprocess.run(["nvidia-smi", f"--id={c}", "--query-gpu=index",
+                                  "--format=csv,noheader"], capture_output=True, text=True,
+                                 timeout=20)
+            if out.returncode == 0 and out.stdout.strip():
+                return c
+        except Exception:
+            pass
+    return cands[-1]
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons.  Each sample carries
     nvidia-smi's own timestamp, so only the samples taken between begin() and
@@ -158,7 +188,7 @@ class ClockSampler:
                 "reasons": sorted(set().union(*[r[3] for r in use])) if use else [],
                 "samples": len(use),
                 "window": "timed steps" if inside else "whole run (no sample inside the timed steps)",
-                "period_ms": self.period_ms}
+                "period_ms": self.period_ms, "gpu": str(self.index)}
 
 
 # ---------------------------------------------------------------- CPU oracle timing
@@ -299,7 +329,7 @@ def run_gpu(args):
         return ms, matches, stats, r, wall
 
     # tensor-core engine (the headline), clocks sampled during the timed steps
-    sampler = ClockSampler(dev.index)
+    sampler = ClockSampler(smi_device_id(dev))
     sampler.start()
     ms_t, m_t, st_t, r_t, wall_t = timed(pkg.ENGINE_TENSOR, args.steps, args.warmup, True, sampler)
     clocks = sampler.stop()
@@ -477,7 +507,7 @@ def run_batch(args):
             sampler.end()
         return ms, out, pkg.fic_stats_read()
 
-    sampler = ClockSampler(dev.index)
+    sampler = ClockSampler(smi_device_id(dev))
     sampler.start()
     ms_b, out_b, st_b = timed(batch, args.steps, args.warmup, True, sampler)
     clocks = sampler.stop()
@@ -553,7 +583,7 @@ def run_serving(args):
             w.poll(w.submit(fic_synth.one_over_f(side, 1, 2.0)))
     srv = pkg.Server(16, 4, 2, 4.0, ss, 8.0, policy=args.policy)
     tickets = [None] * len(imgs)
-    sampler = ClockSampler(dev.index)
+    sampler = ClockSampler(smi_device_id(dev))
     sampler.start()
     sampler.begin()
     t0 = time.perf_counter()

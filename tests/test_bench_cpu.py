@@ -82,3 +82,57 @@ def test_missing_nvidia_smi(tmp_path, monkeypatch):
     s.start()
     c = s.stop()
     assert c["sm_mhz"] is None and c["reasons"] == ["nvidia-smi unavailable"]
+
+
+# A fake nvidia-smi that knows one GPU, physical index 3, by UUID or index.
+FAKE_ID = r'''#!{py}
+import sys
+ids = [a.split("=", 1)[1] for a in sys.argv[1:] if a.startswith("--id=")]
+if ids and ids[0] not in ("GPU-0f0e-test", "3"):
+    print("No devices were found", file=sys.stderr)
+    sys.exit(6)
+print("3")
+'''
+
+
+@pytest.fixture
+def fake_smi_ids(tmp_path, monkeypatch):
+    exe = tmp_path / "nvidia-smi"
+    exe.write_text(FAKE_ID.replace("{py}", sys.executable))
+    exe.chmod(exe.stat().st_mode | stat.S_IXUSR)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ.get("PATH", ""))
+    return exe
+
+
+class _Props:
+    def __init__(self, uuid):
+        self.uuid = uuid
+
+
+def test_clock_id_is_the_device_uuid(fake_smi_ids, monkeypatch):
+    """torch's cuda:0 is physical GPU 3 here; its UUID names it for nvidia-smi,
+    where torch's index 0 would name another GPU."""
+    import torch
+    monkeypatch.setenv("CUDA_VISIBLE_DEVICES", "3")
+    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda d: _Props("0f0e-test"))
+    assert bench.smi_device_id(torch.device("cuda", 0)) == "GPU-0f0e-test"
+
+
+def test_clock_id_from_visible_devices(fake_smi_ids, monkeypatch):
+    """Without a UUID the CUDA_VISIBLE_DEVICES entry of the device is used."""
+    import torch
+
+    def no_props(d):
+        raise RuntimeError("no device")
+    monkeypatch.setenv("CUDA_VISIBLE_DEVICES", "5,3")
+    monkeypatch.setattr(torch.cuda, "get_device_properties", no_props)
+    assert bench.smi_device_id(torch.device("cuda", 1)) == "3"
+
+
+def test_clock_id_falls_back_to_the_index(tmp_path, monkeypatch):
+    """No nvidia-smi at all: torch's index, and the sampler reports it unavailable."""
+    import torch
+    monkeypatch.setenv("PATH", str(tmp_path))
+    monkeypatch.delenv("CUDA_VISIBLE_DEVICES", raising=False)
+    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda d: _Props(""))
+    assert bench.smi_device_id(torch.device("cuda", 0)) == "0"
