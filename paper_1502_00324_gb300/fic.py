@@ -165,13 +165,39 @@ def _check(st, what):
         raise FicError(st, what)
 
 
-def _ptr(x):
-    """(address, keepalive) of a numpy array or torch tensor."""
+def _buf(x, what, min_bytes=0, u8=False, itemsize=None):
+    """(address, keepalive, bytes) of a C-contiguous numpy array or torch
+    tensor.  The library reads and writes these buffers by the sizes passed
+    beside them, so a strided view, an image of another element type or a
+    buffer shorter than ``min_bytes`` is refused here: it would otherwise be
+    read or written past its end, on the host or on the device."""
     if isinstance(x, np.ndarray):
-        return x.ctypes.data, x
-    if hasattr(x, "data_ptr"):
-        return x.data_ptr(), x
-    raise TypeError(f"expected numpy array or torch tensor, got {type(x)}")
+        contig, nbytes, isz = x.flags.c_contiguous, x.nbytes, x.itemsize
+        is_u8 = x.dtype == np.uint8
+        addr = x.ctypes.data
+    elif hasattr(x, "data_ptr"):
+        contig, isz = x.is_contiguous(), x.element_size()
+        nbytes = x.numel() * isz
+        is_u8 = str(x.dtype) == "torch.uint8"
+        addr = x.data_ptr()
+    else:
+        raise TypeError(f"{what}: expected a numpy array or torch tensor, got {type(x)}")
+    if not contig:
+        raise ValueError(f"{what}: the buffer must be C-contiguous")
+    if u8 and not is_u8:
+        raise TypeError(f"{what}: expected uint8 elements, got {x.dtype}")
+    if itemsize is not None and isz != itemsize:
+        raise TypeError(f"{what}: expected {itemsize}-byte elements, got {x.dtype}")
+    if nbytes < min_bytes:
+        raise ValueError(f"{what}: {nbytes} bytes, at least {min_bytes} needed")
+    return addr, x, nbytes
+
+
+def _square_side(img, what):
+    """Side of a square 2-D image (batch and server take N from the shape)."""
+    if len(img.shape) != 2 or img.shape[0] != img.shape[1]:
+        raise ValueError(f"{what}: expected a square 2-D image, got shape {tuple(img.shape)}")
+    return int(img.shape[0])
 
 
 def _stream(stream):
@@ -185,7 +211,11 @@ def _stream(stream):
 def make_ssets(ssets):
     """[(q, [p...]), ...] (one per quadtree step) -> FicSset array."""
     arr = (FicSset * MAX_LEVELS)()
+    if len(ssets) > MAX_LEVELS:
+        raise ValueError(f"{len(ssets)} S sets, at most {MAX_LEVELS} quadtree steps")
     for i, (q, ps) in enumerate(ssets):
+        if len(ps) > MAX_S:
+            raise ValueError(f"S set {i}: {len(ps)} values, at most {MAX_S}")
         arr[i].n_s = len(ps)
         arr[i].q = q
         for j, p in enumerate(ps):
@@ -236,12 +266,11 @@ def fic_encode_ex(img, N, B_max, B_min, L, entropy_thresh, ssets, err_tol,
     records receiving the codes (host or device); otherwise a host array is
     returned."""
     p = make_params(N, B_max, B_min, L, entropy_thresh, ssets, err_tol, engine, pool_dn)
-    ip, keep = _ptr(img)
+    ip, keep, _ = _buf(img, "img", N * N, u8=True)
     res = FicResult()
     if codes_out is not None:
-        cp, keep2 = _ptr(codes_out)
-        cap = (codes_out.nbytes if isinstance(codes_out, np.ndarray)
-               else codes_out.numel() * codes_out.element_size()) // 16
+        cp, keep2, nb = _buf(codes_out, "codes_out")
+        cap = nb // 16
         st = lib().fic_encode_ex(ip, C.byref(p), cp, cap, C.byref(res), _stream(stream))
         _check(st, "fic_encode_ex")
         return Encoded(res, codes_out)
@@ -263,10 +292,11 @@ def fic_encode_batch(imgs, B_max, B_min, L, entropy_thresh, ssets, err_tol,
     Ns = (C.c_int * n)()
     keep = []
     for i, im in enumerate(imgs):
-        ip, k = _ptr(im)
+        side = _square_side(im, f"imgs[{i}]")
+        ip, k, _ = _buf(im, f"imgs[{i}]", side * side, u8=True)
         keep.append(k)
         ptrs[i] = ip
-        Ns[i] = int(im.shape[0])
+        Ns[i] = side
     outs = (FicResult * n)()
     st = lib().fic_encode_batch(n, C.cast(ptrs, C.c_void_p), C.cast(Ns, C.c_void_p), C.byref(p),
                                 outs, _stream(stream))
@@ -295,7 +325,7 @@ def _adopt(res: FicResult) -> Encoded:
 
 def fic_encode(img, N, B_max, B_min, L, entropy_thresh, ssets, err_tol, stream=None):
     """fic_encode of include/fic.h (tensor-core engine, host codes)."""
-    ip, keep = _ptr(img)
+    ip, keep, _ = _buf(img, "img", N * N, u8=True)
     res = FicResult()
     ss = make_ssets(ssets)
     st = lib().fic_encode(ip, N, B_max, B_min, L, float(entropy_thresh), ss, float(err_tol),
@@ -309,7 +339,7 @@ def fic_pack(img, enc: Encoded, B_max, B_min, L, entropy_thresh, ssets, err_tol,
     """The stored stream of an encode (bytes) and its record bits alone; the
     arguments after ``enc`` are the encode's parameters."""
     p = make_params(enc.N, B_max, B_min, L, entropy_thresh, ssets, err_tol, engine, pool_dn)
-    ip, keep = _ptr(img)
+    ip, keep, _ = _buf(img, "img", enc.N * enc.N, u8=True)
     nb = C.c_int64(0)
     pb = C.c_int64(0)
     _check(lib().fic_pack(ip, C.byref(p), C.byref(enc._res), None, 0, C.byref(nb), C.byref(pb),
@@ -325,7 +355,7 @@ def fic_decode(enc: Encoded, iters_max=64, out=None, stream=None):
     N = enc.N
     if out is None:
         out = np.empty((N, N), np.uint8)
-    op, keep = _ptr(out)
+    op, keep, _ = _buf(out, "out", N * N, u8=True)
     used = C.c_int(0)
     st = lib().fic_decode(C.byref(enc._res), N, iters_max, op, C.byref(used), _stream(stream))
     _check(st, "fic_decode")
@@ -335,7 +365,7 @@ def fic_decode(enc: Encoded, iters_max=64, out=None, stream=None):
 def fic_domain_pool(img, N, B, L, entropy_thresh, stream=None, pool_dn=0):
     """Kernels (a)+(b) alone: (pool positions (DN, 2), entropy per position,
     near-threshold count); pool_dn > 0: the top-DN rule."""
-    ip, keep = _ptr(img)
+    ip, keep, _ = _buf(img, "img", N * N, u8=True)
     per = (N - 2 * B) // L + 1 if N >= 2 * B else 0
     npos = per * per
     ent = np.empty(max(npos, 1), np.float64)
@@ -404,10 +434,13 @@ def fic_domain_pool_noalloc(d_img, N, B, L, entropy_thresh, d_pool_xy, d_entropy
     buffers are the caller's device tensors (``d_pool_xy``: int32/uint32
     tensor receiving packed x | y << 16; ``d_entropy``: float64 tensor or
     None).  Returns (pool size, near-threshold count)."""
-    ip, keep = _ptr(d_img)
-    pp, keep2 = _ptr(d_pool_xy)
-    cap = d_pool_xy.numel()
-    ep = d_entropy.data_ptr() if d_entropy is not None else None
+    ip, keep, _ = _buf(d_img, "d_img", N * N, u8=True)
+    pp, keep2, nb = _buf(d_pool_xy, "d_pool_xy", itemsize=4)
+    cap = nb // 4
+    ep = None
+    if d_entropy is not None:
+        per = (N - 2 * B) // L + 1 if N >= 2 * B and L > 0 else 0
+        ep, keep3, _ = _buf(d_entropy, "d_entropy", 8 * per * per, itemsize=8)
     dn = C.c_int64(0)
     near = C.c_int64(0)
     st = lib().fic_domain_pool_noalloc(ip, N, B, L, float(entropy_thresh), pp, cap, C.byref(dn),
@@ -436,9 +469,10 @@ class Server:
         self._keep = {}
 
     def submit(self, img):
-        ip, keep = _ptr(img)
+        side = _square_side(img, "img")
+        ip, keep, _ = _buf(img, "img", side * side, u8=True)
         t = C.c_int64(0)
-        st = lib().fic_server_submit(self._h, ip, int(img.shape[0]), C.byref(t))
+        st = lib().fic_server_submit(self._h, ip, side, C.byref(t))
         _check(st, "fic_server_submit")
         if not isinstance(img, np.ndarray):
             self._keep[t.value] = keep

@@ -63,7 +63,7 @@ def test_bad_arguments_rejected_on_host(fic, bad):
     args = dict(N=64, B_max=16, B_min=4, L=1, thr=-1.0, err_tol=8.0,
                 ssets=[(10, [1]), (10, [2, 4]), (10, [3, 8])], engine=0, pool_dn=0)
     args.update(bad)
-    img = np.zeros((64, 64), np.uint8)
+    img = np.zeros((args["N"], args["N"]), np.uint8)
     with pytest.raises(fic.FicError) as e:
         fic.fic_encode_ex(img, args["N"], args["B_max"], args["B_min"], args["L"], args["thr"],
                           args["ssets"], args["err_tol"], engine=args["engine"],
@@ -90,3 +90,47 @@ def test_process_modes_set_and_read_on_host(fic):
     assert e.value.status == fic.fic.FIC_EINVAL
     t = fic.fic_tune_mode(0)
     assert fic.fic_tune_mode(t) == 0
+
+
+SS3 = [(10, [1]), (10, [2, 4]), (10, [3, 8])]
+
+
+def test_binding_refuses_buffers_the_library_would_overrun(fic):
+    """The library reads an N x N image and writes records, pool entries and
+    entropies by the sizes passed beside the pointers; the binding refuses a
+    buffer that is shorter, strided or of another element type before any
+    call, so no such pointer reaches the host code or a kernel."""
+    import torch
+    f = fic.fic
+    img = np.zeros((64, 64), np.uint8)
+    with pytest.raises(ValueError, match="at least 16384"):
+        f.fic_encode_ex(img, 128, 16, 4, 1, -1.0, SS3, 8.0)          # N larger than the buffer
+    wide = np.zeros((64, 128), np.uint8)
+    with pytest.raises(ValueError, match="contiguous"):
+        f.fic_encode_ex(wide[:, ::2], 64, 16, 4, 1, -1.0, SS3, 8.0)   # strided view
+    with pytest.raises(TypeError, match="uint8"):
+        f.fic_encode_ex(img.astype(np.int16), 64, 16, 4, 1, -1.0, SS3, 8.0)
+    with pytest.raises(ValueError, match="contiguous"):
+        f.fic_encode(torch.zeros(64, 64, dtype=torch.uint8).t()[:, :32], 64, 16, 4, 1, -1.0, SS3,
+                     8.0)
+    with pytest.raises(ValueError, match="square"):
+        f.fic_encode_batch([img, np.zeros((64, 32), np.uint8)], 16, 4, 1, -1.0, SS3, 8.0)
+    with pytest.raises(ValueError, match="at least"):
+        f.fic_domain_pool(img[:32], 64, 8, 2, -1.0)
+    # allocation-free pool: entries are 4 bytes, entropies 8 bytes per position
+    with pytest.raises(TypeError, match="4-byte"):
+        f.fic_domain_pool_noalloc(img, 64, 8, 2, -1.0, np.zeros(1024, np.uint8))
+    xy = np.zeros(1024, np.int32)
+    with pytest.raises(TypeError, match="8-byte"):
+        f.fic_domain_pool_noalloc(img, 64, 8, 2, -1.0, xy, np.zeros(625, np.float32))
+    with pytest.raises(ValueError, match="at least 5000"):                # (64-16)/2+1 = 25
+        f.fic_domain_pool_noalloc(img, 64, 8, 2, -1.0, xy, np.zeros(624, np.float64))
+
+
+def test_binding_refuses_oversize_S_sets(fic):
+    f = fic.fic
+    with pytest.raises(ValueError, match="at most 16"):
+        f.make_ssets([(64, list(range(17)))])
+    with pytest.raises(ValueError, match="at most 4"):
+        f.make_ssets([(10, [1])] * 5)
+    assert f.make_ssets([(10, list(range(16)))])[0].n_s == 16
