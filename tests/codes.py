@@ -40,3 +40,15 @@ def to_oracle_records(codes: np.ndarray, B_max: int):
     for f in FIELDS + ("B",):
         out[f] = g[f]
     return out
+
+
+DIGEST_FIELDS = ("rx", "ry", "level", "B", "iso", "s_idx", "o_q", "dx", "dy", "pool_idx")
+
+
+def field_digests(common: dict) -> dict:
+    """SHA-256 of each record field as int64 little-endian, in record order
+    (a mean-only record's S index as -1): the form in which the oracle's
+    full-size encodes are stored under tests/golden/."""
+    import hashlib
+    return {f: hashlib.sha256(np.ascontiguousarray(common[f], dtype="<i8").tobytes()).hexdigest()
+            for f in DIGEST_FIELDS}

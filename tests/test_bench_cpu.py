@@ -136,3 +136,40 @@ def test_clock_id_falls_back_to_the_index(tmp_path, monkeypatch):
     monkeypatch.delenv("CUDA_VISIBLE_DEVICES", raising=False)
     monkeypatch.setattr(torch.cuda, "get_device_properties", lambda d: _Props(""))
     assert bench.smi_device_id(torch.device("cuda", 0)) == "0"
+
+
+def test_reference_arm_weights_step_rates_by_the_encode(monkeypatch, capsys):
+    """The reference line's value is the whole-encode rate: each quadtree
+    step's sampled oracle rate weighted by that step's matches in the
+    oracle's full encode, not the raw sum over the sample."""
+    import argparse
+    import json as _json
+    rates = [1e7, 4e7, 1e8]                       # matches per second at B = 16, 8, 4
+
+    def fake_sample(img, ss, per_level=(0, 0, 0), seed=0, nthreads=0):
+        m, s, d = 0, 0.0, []
+        for lvl, k in enumerate(per_level):
+            if k:
+                mm = k * 1000 * 8
+                m += mm
+                s += mm / rates[lvl]
+                d.append(f"{k} ranges at level {lvl}")
+        return m, s, "; ".join(d)
+
+    weights = [2e9, 8e9, 3e10]
+    monkeypatch.setattr(bench, "oracle_sample", fake_sample)
+    monkeypatch.setattr(bench, "oracle_encode_matches", lambda: [int(w) for w in weights])
+    args = argparse.Namespace(steps=2, warmup=3, gpus=1)
+    assert bench.run_reference(args) == 0
+    line = _json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    want = sum(weights) / sum(w / r for w, r in zip(weights, rates)) / 1e9
+    assert line["impl"] == "reference"
+    assert abs(line["value"] - want) < 1e-12 * want
+    assert line["cpu_baseline"]["value"] == line["value"] == line["e2e"]["value"]
+    assert "oracle's full encode" in line["cpu_baseline"]["sample"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_stored_oracle_counts_are_read():
+    m = bench.oracle_encode_matches()
+    assert m is not None and len(m) == 3 and all(x > 0 for x in m)
