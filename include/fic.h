@@ -426,6 +426,24 @@ const char* fic_version(void);
  * returned on this thread ("" if none).  Static per-thread storage. */
 const char* fic_last_error(void);
 
+/* fic_wait_selftest -- a check of the library's failure handling; the paper
+ * has no counterpart.  Runs the bounded mbarrier wait that every tensor-core
+ * kernel uses, in a one-warp kernel on the current device:
+ *   complete      nonzero: the barrier's phase completes before the wait
+ *                 (the wait succeeds); 0: nothing ever arrives, so the wait
+ *                 runs until its limit and gives up.
+ *   limit_cycles  the wait's limit in SM clock cycles, 1 ..
+ *                 FIC_SELFTEST_MAX_CYCLES (about 2 s at 2 GHz); the clock is
+ *                 read every 16 polls of at most 1 ms each.
+ *   stream        CUDA stream (NULL = default); the call synchronises it.
+ * Returns FIC_OK when the wait saw the phase, FIC_ETIMEOUT when it gave up
+ * (the kernel returned early and the context stays usable, as after an
+ * encode's timeout), FIC_EINVAL for a limit out of range, FIC_ENODEV without
+ * an sm_103 device, FIC_ECUDA on a CUDA error.  The error word is shared by
+ * all calls: calls that overlap on the GPU race. */
+#define FIC_SELFTEST_MAX_CYCLES 4000000000LL
+int fic_wait_selftest(int complete, int64_t limit_cycles, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

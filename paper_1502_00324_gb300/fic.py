@@ -95,7 +95,7 @@ EXPORTS = ["fic_encode", "fic_encode_ex", "fic_encode_batch", "fic_decode", "fic
            "fic_strerror", "fic_stats_reset", "fic_stats_read", "fic_version",
            "fic_domain_pool_noalloc", "fic_last_error", "fic_pack", "fic_tune_mode",
            "fic_tune_read", "fic_graph_mode", "fic_graph_counts", "fic_server_create", "fic_server_submit",
-           "fic_server_poll", "fic_server_stats_read", "fic_server_destroy"]
+           "fic_server_poll", "fic_server_stats_read", "fic_server_destroy", "fic_wait_selftest"]
 
 
 class FicError(RuntimeError):
@@ -152,6 +152,7 @@ def lib():
                                   C.POINTER(FicTiming)]
     L.fic_server_stats_read.argtypes = [vp, C.POINTER(FicServerStats)]
     L.fic_server_destroy.argtypes = [vp]
+    L.fic_wait_selftest.argtypes = [C.c_int, C.c_int64, vp]
     _lib = L
     return L
 
@@ -422,6 +423,13 @@ def fic_stats_read():
     return {k: dict(launches=int(s.launches[i]), ms=float(s.ms[i]), flops=float(s.flops[i]),
                     bytes=float(s.bytes[i])) for i, k in enumerate(KERNEL_KINDS)} | {
         "matches": int(s.matches)}
+
+
+def fic_wait_selftest(complete, limit_cycles, stream=None):
+    """The tensor kernels' bounded mbarrier wait on its own (include/fic.h):
+    returns the library status, FIC_OK when the phase completed, FIC_ETIMEOUT
+    when the wait gave up at its limit."""
+    return lib().fic_wait_selftest(1 if complete else 0, int(limit_cycles), _stream(stream))
 
 
 def fic_version():

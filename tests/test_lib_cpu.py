@@ -134,3 +134,18 @@ def test_binding_refuses_oversize_S_sets(fic):
     with pytest.raises(ValueError, match="at most 4"):
         f.make_ssets([(10, [1])] * 5)
     assert f.make_ssets([(10, list(range(16)))])[0].n_s == 16
+
+
+def test_wait_selftest_host_checks(fic):
+    """The limit is checked before the device: out of range is FIC_EINVAL; in
+    range, a machine without an sm_103 device gets FIC_ENODEV."""
+    f = fic.fic
+    assert f.fic_wait_selftest(False, 0) == f.FIC_EINVAL
+    assert f.fic_wait_selftest(False, 4_000_000_001) == f.FIC_EINVAL
+    try:
+        import torch
+        has_dev = torch.cuda.is_available()
+    except Exception:
+        has_dev = False
+    if not has_dev:
+        assert f.fic_wait_selftest(False, 1000) == f.FIC_ENODEV
