@@ -44,6 +44,14 @@
  *     mean-only record (pool index 0xFFFFFFFF);
  *   - decoding starts from a constant 128 image and applies all mappings to
  *     the previous iterate (Jacobi) until a fixed point or a cap.
+ *
+ * Parity status: every function here is pinned by tests that do not use
+ * the oracle's own formulas (tests/test_oracle_pins.py: brute force, exact
+ * rationals, closed forms, library routines, the paper's printed counts);
+ * the pins are themselves checked by planting mistakes in copies of this
+ * file (tests/test_oracle_mutations.py).  Parity unpinned: the absolute
+ * quality of an encode (PSNR, compression ratio) against the paper's
+ * tables, whose test images are not available.
  */
 #include <math.h>
 #include <stdint.h>
