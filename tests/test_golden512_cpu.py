@@ -74,3 +74,30 @@ def test_gpu_record_format_gives_the_oracle_digests():
     bad["iso"][len(bad) // 2] ^= 1
     got = field_digests(oracle_to_common(bad))
     assert [f for f in got if got[f] != want[f]] == ["iso"]
+
+
+GOLD_B64 = os.path.join(HERE, "golden", "batch64_oracle.json")
+
+
+def test_stored_batch_encodes_cover_the_small_images_of_the_workload():
+    gold = json.load(open(GOLD_B64))
+    gw = gold["workload"]
+    imgs = fic_synth.batch_images(gw["count"], gw["seed0"])
+    want = [i for i, im in enumerate(imgs) if im.shape[0] <= gw["max_side"]]
+    assert [g["index"] for g in gold["images"]] == want and len(want) > 0
+    for g in gold["images"]:
+        img = imgs[g["index"]]
+        assert g["N"] == img.shape[0] and g["seed"] == gw["seed0"] + g["index"]
+        assert hashlib.sha256(np.ascontiguousarray(img).tobytes()).hexdigest() == \
+            g["image_sha256"]
+        N, L = g["N"], gw["L"]
+        sides = [gw["B_max"] >> l for l in range(len(g["ranges"]))]
+        assert sides[-1] == gw["B_min"]
+        assert g["ranges"][0] == (N // gw["B_max"]) ** 2
+        for l, B in enumerate(sides):   # entropy-filtered pools within the positions
+            assert 0 <= g["pool_size"][l] <= ((N - 2 * B) // L + 1) ** 2
+        for l in range(len(sides) - 1):  # split ranges have four children each
+            assert g["ranges"][l + 1] % 4 == 0 and g["ranges"][l + 1] <= 4 * g["ranges"][l]
+        # every range of the last step is kept; the steps before keep the rest
+        kept = sum(g["ranges"][l] - g["ranges"][l + 1] // 4 for l in range(len(sides) - 1))
+        assert g["n_records"] == kept + g["ranges"][-1]
