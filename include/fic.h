@@ -305,7 +305,9 @@ int fic_server_create(const fic_params* p, const fic_server_config* cfg, fic_ser
  * complete on the device before the call, e.g. its producing stream
  * synchronised, and stay valid and unchanged until the ticket completes;
  * the server reads it from its own stream).  *ticket receives an id > 0.
- * FIC_EINVAL: N invalid for the parameter set; FIC_EBUSY: queue full. */
+ * FIC_EINVAL: N invalid for the parameter set; FIC_EBUSY: queue full, or
+ * the server stopped (destroyed, or its worker failed: then every queued and
+ * running request completes with FIC_ENOMEM). */
 int fic_server_submit(fic_server* s, const uint8_t* img, int N, int64_t* ticket);
 /* fic_server_poll -- wait up to wait_ms (0: do not wait, < 0: forever) for
  * a ticket.  FIC_OK: *out receives the result (host codes owned by the

@@ -182,6 +182,26 @@ struct fic_server {
         cv_done.notify_all();
     }
 
+    // The worker's last act when its loop ends on an exception: every
+    // request it holds or has queued fails with `status`, waiting polls wake,
+    // and later submits are refused (the server takes no more work).
+    void fail_all_and_stop(int status)
+    {
+        std::lock_guard<std::mutex> g(mu);
+        stop = true;
+        for (auto& f : inflight) finish_one(f, status);
+        inflight.clear();
+        while (!queue.empty()) {
+            std::unique_ptr<InFlight> f(new InFlight());
+            f->req = std::move(queue.front());
+            queue.pop_front();
+            finish_one(f, status, false);
+        }
+        st.inflight = 0;
+        st.queued = 0;
+        cv_done.notify_all();
+    }
+
     void run()
     {
         cudaSetDevice(device);
@@ -330,7 +350,10 @@ int fic_server_create(const fic_params* p, const fic_server_config* cfg, fic_ser
             try {
                 raw->run();
             } catch (...) {
-                raw->fail_all_inflight(FIC_ENOMEM);
+                try {
+                    raw->fail_all_and_stop(FIC_ENOMEM);
+                } catch (...) {
+                }
             }
         });
         *out = s.release();
