@@ -13,6 +13,8 @@ import numpy as np
 import pytest
 
 import fic_synth
+import oracle
+from tests.codes import assert_same_codes
 
 pytestmark = pytest.mark.gpu
 
@@ -79,6 +81,11 @@ def test_mix_equals_alone_with_staggered_arrivals(pkg):
         assert tm["submit_ms"] <= tm["admit_ms"] <= tm["done_ms"]
         assert 1 <= tm["steps"] <= 3
         shared += tm["shared_steps"]
+        if imgs[i].shape[0] <= 128:  # small enough for the oracle in about a second
+            ss = pkg.paper_ssets(ARGS["B_max"], ARGS["B_min"])
+            ref, _ = oracle.encode(imgs[i], ARGS["B_max"], ARGS["B_min"], ARGS["L"],
+                                   ARGS["entropy_thresh"], ss, ARGS["err_tol"])
+            assert_same_codes(enc.codes, ref, ARGS["B_max"], f"served request {i}")
     st = srv.stats()
     srv.close()
     assert st["completed"] == len(imgs) and st["failed"] == 0
