@@ -10,6 +10,10 @@ side, SHA-256 of the pixels, per-step counts and one SHA-256 per record field
 (int64 little-endian, in record order, a mean-only record's S index as -1).
 
     python tests/golden/make_batch64.py [--max-side 256] [--threads T]
+    python tests/golden/make_batch64.py --add 3,4   # append images 3 and 4
+
+``--add`` keeps the stored images and appends the oracle's encodes of the
+listed image indices (of any side); ``extra_indices`` in the file lists them.
 """
 from __future__ import annotations
 
@@ -36,13 +40,46 @@ B_MAX, B_MIN, L, THR, TOL = 16, 4, 2, 4.0, 8.0
 SEED0, COUNT = 100, 64
 
 
+def encode_one(imgs, i, ss, threads):
+    """The oracle's full encode of image i, as stored."""
+    img = imgs[i]
+    n = int(img.shape[0])
+    t0 = time.time()
+    codes, st = oracle.encode(img, B_MAX, B_MIN, L, THR, ss, TOL, nthreads=threads)
+    rec = {
+        "index": i, "seed": SEED0 + i, "N": n,
+        "image_sha256": hashlib.sha256(np.ascontiguousarray(img).tobytes()).hexdigest(),
+        "ranges": [int(x) for x in st["ranges"]],
+        "pool_size": [int(x) for x in st["pool_size"]],
+        "n_records": int(len(codes)),
+        "field_sha256": field_digests(oracle_fields(codes)),
+        "oracle_seconds": round(time.time() - t0, 2),
+    }
+    print(i, n, len(codes), round(time.time() - t0, 1), flush=True)
+    return rec
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--max-side", type=int, default=256)
     ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--add", default="")
     args = ap.parse_args()
     ss = [PAPER_S[b] for b in (16, 8, 4)]
     imgs = fic_synth.batch_images(COUNT, SEED0)
+    if args.add:
+        add = [int(x) for x in args.add.split(",")]
+        out = json.load(open(OUT))
+        have = {g["index"] for g in out["images"]}
+        for i in add:
+            if i not in have:
+                out["images"].append(encode_one(imgs, i, ss, args.threads))
+        out["images"].sort(key=lambda g: g["index"])
+        out["extra_indices"] = sorted(set(out.get("extra_indices", [])) | set(add))
+        with open(OUT, "w") as f:
+            json.dump(out, f, indent=1)
+            f.write("\n")
+        return
     out = {
         "_about": ("Oracle full encodes of the 64-image batching workload's images of side "
                    f"<= {args.max_side}; written by tests/golden/make_batch64.py from oracle/ "
@@ -54,21 +91,8 @@ def main():
     }
     t_all = time.time()
     for i, img in enumerate(imgs):
-        n = int(img.shape[0])
-        if n > args.max_side:
-            continue
-        t0 = time.time()
-        codes, st = oracle.encode(img, B_MAX, B_MIN, L, THR, ss, TOL, nthreads=args.threads)
-        out["images"].append({
-            "index": i, "seed": SEED0 + i, "N": n,
-            "image_sha256": hashlib.sha256(np.ascontiguousarray(img).tobytes()).hexdigest(),
-            "ranges": [int(x) for x in st["ranges"]],
-            "pool_size": [int(x) for x in st["pool_size"]],
-            "n_records": int(len(codes)),
-            "field_sha256": field_digests(oracle_fields(codes)),
-            "oracle_seconds": round(time.time() - t0, 2),
-        })
-        print(i, n, len(codes), round(time.time() - t0, 1), flush=True)
+        if int(img.shape[0]) <= args.max_side:
+            out["images"].append(encode_one(imgs, i, ss, args.threads))
     out["oracle_seconds_total"] = round(time.time() - t_all, 1)
     out["oracle_threads"] = int(args.threads or oracle.max_threads())
     with open(OUT, "w") as f:
