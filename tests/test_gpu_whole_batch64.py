@@ -1,6 +1,6 @@
 """The 64-image batching workload in the launch configuration the benchmark
 times (all 64 images in one fic_encode_batch call), against the oracle's own
-full encodes of its images of side <= 384 and two of side 512 (36 of the 64).
+full encodes of its images of side <= 384 and four of side 512 (38 of the 64).
 
 Those encodes are stored as per-field SHA-256 digests with per-step counts in
 tests/golden/batch64_oracle.json, written by tests/golden/make_batch64.py
