@@ -205,17 +205,19 @@ int fic_domain_pool(const uint8_t* img, int N, int B, int L, double entropy_thre
  * call allocates nothing (no cudaMalloc, cudaFree or allocating library
  * routine); the caller passes device buffers for the input and the outputs,
  * and the intermediates live in one static device array of the library
- * (about 8.1 MB per GPU, held until the process exits).
+ * (8,398,592 bytes = 8.0 MiB per GPU, held until the process exits).
  *   d_img      device, N*N bytes, read only.
  *   d_pool_xy  device, cap uint32 entries: admitted positions in raster
  *              order, packed x | (y << 16).  May be NULL with cap 0.
  *   dn, near   host outputs: pool size; positions with |H - thr| < 1e-9.
  *   d_entropy  device, n_positions doubles (eq. 5-6, bits), or NULL.
- * Returns FIC_EINVAL when n_positions = ((N-2B)/L+1)^2 exceeds
- * FIC_NOALLOC_MAX_POSITIONS or a buffer is not device memory, FIC_ECAP
- * (with *dn set) when cap < DN.  The first call on each device sets the
- * scratch up (symbol lookup and a table kernel): make it before any stream
- * capture.  Calls share the scratch: calls that overlap on the GPU race. */
+ * Returns FIC_EINVAL when N > 65535, when n_positions = ((N-2B)/L+1)^2
+ * exceeds FIC_NOALLOC_MAX_POSITIONS or a buffer is not device memory,
+ * FIC_ECAP (with *dn set) when cap < DN.  Every call looks the scratch's
+ * device address up; the first call on each device (and the first after a
+ * device reset) also fills a table with one kernel and waits for it: make
+ * that call before any stream capture.  Calls share the scratch: calls that
+ * overlap on the GPU race. */
 #define FIC_NOALLOC_MAX_POSITIONS (1 << 20)
 int fic_domain_pool_noalloc(const uint8_t* d_img, int N, int B, int L,
                             double entropy_thresh, uint32_t* d_pool_xy, int64_t cap,

@@ -48,15 +48,25 @@ CODE_DTYPE = np.dtype([("rx", np.int32), ("ry", np.int32), ("level", np.int32),
 assert CODE_DTYPE.itemsize == C.sizeof(OrCode)
 
 _lib = None
+_path = None
+
+
+def use_library(path):
+    """Load the build of the oracle at ``path`` instead of the default one.
+    Only the pins' mutation test does this, passing a copy with a planted
+    mistake explicitly (pytest's --oracle-lib option); it must come before
+    the first call into the oracle."""
+    global _path
+    if _lib is not None:
+        raise RuntimeError("the oracle library is already loaded")
+    _path = os.path.abspath(path)
 
 
 def lib():
-    """The compiled oracle.  FIC_ORACLE_LIB names another build of the same
-    source to load instead: the pins' mutation test runs them against copies
-    of the oracle with a planted mistake."""
+    """The compiled oracle (built from oracle/fic_oracle.c on first use)."""
     global _lib
     if _lib is None:
-        path = os.environ.get("FIC_ORACLE_LIB") or _build()
+        path = _path or _build()
         L = C.CDLL(path)
         u8p = C.POINTER(C.c_uint8)
         i32p = C.POINTER(C.c_int32)

@@ -294,8 +294,16 @@ int fic_domain_pool(const uint8_t* img, int N, int B, int L, double entropy_thre
                     int64_t pool_dn, int32_t* pool_xy, int64_t cap, int64_t* dn,
                     double* entropy, int64_t* near, void* stream)
 {
+    g_last_error[0] = '\0';
     if (!img || !dn || N <= 0 || N > 65535 || !valid_side(B) || L < 1 || pool_dn < 0)
         return FIC_EINVAL;
+    const int64_t per_axis = positions_per_axis(N, B, L);
+    if (per_axis * per_axis > kMaxScanCount) {
+        snprintf(g_last_error, sizeof(g_last_error),
+                 "%lld domain positions exceed the scan limit of %lld",
+                 (long long)(per_axis * per_axis), (long long)kMaxScanCount);
+        return FIC_EINVAL;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     Context* c = nullptr;
     int st = get_context(&c, s);

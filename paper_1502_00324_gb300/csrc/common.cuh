@@ -93,6 +93,15 @@ __host__ __device__ inline unsigned pack_idx(unsigned c, unsigned k, unsigned s)
     return (c << 7) | (k << 4) | s;
 }
 
+// The key keeps 25 bits for the pool index, so a step's padded pool must
+// stay within 2^25 columns; validate_params rejects larger pools.
+constexpr int64_t kMaxPoolColumns = (int64_t)1 << 25;
+// The device-wide scan (pool compaction, split requeue, record order) takes
+// at most kMaxScanTiles tiles of kScanTileItems elements.
+constexpr int64_t kScanTileItems = 4096;
+constexpr int64_t kMaxScanTiles = 4096;
+constexpr int64_t kMaxScanCount = kScanTileItems * kMaxScanTiles;
+
 __device__ __forceinline__ bool key_less(long long h1, unsigned i1, long long h2, unsigned i2)
 {
     return h1 < h2 || (h1 == h2 && i1 < i2);

@@ -194,6 +194,7 @@ void set_tune_mode(int mode) { g_tune_mode.store(mode); }
 
 int validate_params(const fic_params* p, int N, int* n_levels)
 {
+    g_last_error[0] = '\0';
     if (!p) return FIC_EINVAL;
     if (N <= 0 || N > 65535) return FIC_EINVAL;
     if (!valid_side(p->B_max) || !valid_side(p->B_min) || p->B_min > p->B_max) return FIC_EINVAL;
@@ -211,7 +212,43 @@ int validate_params(const fic_params* p, int N, int* n_levels)
         for (int i = 0; i < s.n_s; ++i)
             if (s.p[i] < 0 || s.p[i] > s.q) return FIC_EINVAL;
     }
+    const int st = check_size_limits(*p, N, nl);
+    if (st) return st;
     *n_levels = nl;
+    return FIC_OK;
+}
+
+int check_size_limits(const fic_params& p, int N, int nl)
+{
+    const bool listed = p.entropy_thresh >= 0.0 || p.pool_dn > 0;
+    for (int lvl = 0; lvl < nl; ++lvl) {
+        const int B = p.B_max >> lvl;
+        const int per = positions_per_axis(N, B, p.L);
+        const int64_t npos = (int64_t)per * per;
+        const int64_t dn = p.pool_dn > 0 && p.pool_dn < npos ? p.pool_dn : npos;
+        const int64_t ranges = (int64_t)(N / B) * (N / B);
+        if (round_up64(dn > 0 ? dn : 1, kColPad) > kMaxPoolColumns) {
+            snprintf(g_last_error, sizeof(g_last_error),
+                     "step %d (B=%d): pool of %lld domains exceeds the %lld-column limit of the "
+                     "argmin key",
+                     lvl, B, (long long)dn, (long long)kMaxPoolColumns);
+            return FIC_EINVAL;
+        }
+        if ((listed && npos > kMaxScanCount) || ranges > kMaxScanCount) {
+            snprintf(g_last_error, sizeof(g_last_error),
+                     "step %d (B=%d): %lld domain positions or %lld ranges exceed the scan "
+                     "limit of %lld",
+                     lvl, B, (long long)npos, (long long)ranges, (long long)kMaxScanCount);
+            return FIC_EINVAL;
+        }
+    }
+    const int64_t cells = (int64_t)(N / p.B_min) * (N / p.B_min);
+    if (cells > kMaxScanCount) {
+        snprintf(g_last_error, sizeof(g_last_error),
+                 "%lld finest cells exceed the scan limit of %lld", (long long)cells,
+                 (long long)kMaxScanCount);
+        return FIC_EINVAL;
+    }
     return FIC_OK;
 }
 

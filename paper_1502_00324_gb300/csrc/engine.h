@@ -163,6 +163,9 @@ int graph_mode();
 void set_graph_mode(int mode);
 
 int validate_params(const fic_params* p, int N, int* n_levels);
+// Pool, range and record counts within the device code's limits
+// (kMaxPoolColumns, kMaxScanCount); FIC_EINVAL with fic_last_error set.
+int check_size_limits(const fic_params& p, int N, int n_levels);
 int positions_per_axis(int N, int B, int L);
 
 class Engine {

@@ -10,16 +10,20 @@
 // the fixed-point q log2 q table, two counters) live in one file-scope static device
 // array instead of the library's allocating workspace.
 //
-// Scratch: FIC_NOALLOC_MAX_POSITIONS (2^20) domain positions, about 8.1 MB
-// per GPU that loads the library, held until the process exits.  Every call
+// Scratch: FIC_NOALLOC_MAX_POSITIONS (2^20) domain positions, 8,398,592
+// bytes (8.0 MiB) per GPU that loads the library, held until the process
+// exits.  Every call
 // shares it and it keeps the last call's contents, so calls that overlap on
 // the GPU (different streams or threads without ordering) race; the counter
 // that accumulates is cleared at the start of each call, everything else is
 // fully overwritten.
 //
-// Set-up: the first call on each device (with that device current) looks up
-// the array's device address with cudaGetSymbolAddress and fills the table
-// with one kernel launch.  Make that first call before any stream capture.
+// Set-up: every call looks up the array's device address on the current
+// device with cudaGetSymbolAddress (a lookup, no allocation).  The first call
+// on a device, and the first call after the module was loaded again (a new
+// context after cudaDeviceReset, where the address can change), fills the
+// table with one kernel launch and waits for it: make that call before any
+// stream capture.
 #include <cstring>
 #include <mutex>
 
@@ -42,13 +46,15 @@ constexpr size_t kOffTable = align256(kOffScan + sizeof(uint32_t) * kScanWords);
 constexpr size_t kOffTotal = align256(kOffTable + sizeof(long long) * kTableCount);
 constexpr size_t kOffNear = kOffTotal + 8;
 constexpr size_t kScratchBytes = align256(kOffNear + 8);
+static_assert(kScratchBytes == 8398592, "scratch size stated in fic.h");
 
 // The scratch.  In host code this name is a host-side stand-in, not a device
 // address: host code must use the address from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
+// The address whose table was filled, per device ordinal.
 struct DeviceSlot {
-    unsigned char* base = nullptr;
+    unsigned char* filled = nullptr;
 };
 std::mutex g_mu;
 DeviceSlot g_slot[64];
@@ -63,7 +69,8 @@ bool on_device(const void* p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-// Once per device: scratch address and the entropy table (no allocation).
+// Scratch address on the current device; the entropy table is filled when
+// this address has not been filled before (no allocation).
 int setup(cudaStream_t s, unsigned char** base)
 {
     int dev = 0;
@@ -73,18 +80,19 @@ int setup(cudaStream_t s, unsigned char** base)
         cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess)
         return FIC_ENODEV;
     if (major != 10 || minor != 3) return FIC_ENODEV;
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return FIC_ECUDA;
+    unsigned char* b = static_cast<unsigned char*>(p);
     std::lock_guard<std::mutex> g(g_mu);
-    if (!g_slot[dev].base) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return FIC_ECUDA;
-        unsigned char* b = static_cast<unsigned char*>(p);
+    if (g_slot[dev].filled != b) {
+        g_slot[dev].filled = nullptr;
         if (launch_entropy_table(reinterpret_cast<long long*>(b + kOffTable), kTableCount, s) !=
             cudaSuccess)
             return FIC_ECUDA;
         if (cudaStreamSynchronize(s) != cudaSuccess) return FIC_ECUDA;
-        g_slot[dev].base = b;
+        g_slot[dev].filled = b;
     }
-    *base = g_slot[dev].base;
+    *base = b;
     return FIC_OK;
 }
 
@@ -98,7 +106,7 @@ extern "C" int fic_domain_pool_noalloc(const uint8_t* d_img, int N, int B, int L
                                        int64_t* dn, double* d_entropy, int64_t* near,
                                        void* stream)
 {
-    if (!d_img || !dn || N <= 0 || L < 1 || cap < 0) return FIC_EINVAL;
+    if (!d_img || !dn || N <= 0 || N > 65535 || L < 1 || cap < 0) return FIC_EINVAL;
     if (!(B == 2 || B == 4 || B == 8 || B == 16)) return FIC_EINVAL;
     if (cap > 0 && !d_pool_xy) return FIC_EINVAL;
     const int per = (N >= 2 * B) ? (N - 2 * B) / L + 1 : 0;

@@ -230,6 +230,7 @@ __global__ void select_flags_kernel(const unsigned long long* __restrict__ keys,
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;
+static_assert(kScanTile == kScanTileItems, "scan tile size");
 
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total)
 {
@@ -338,7 +339,7 @@ cudaError_t launch_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* 
 {
     if (n <= 0) return cudaMemsetAsync(total, 0, sizeof(uint32_t), s);
     const int64_t nb = (n + kScanTile - 1) / kScanTile;
-    if (nb > 4096) return cudaErrorInvalidValue;
+    if (nb > kMaxScanTiles) return cudaErrorInvalidValue;
     scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, n_dev, tmp);
     scan_top_kernel<<<1, 1024, 0, s>>>(tmp, (int)nb, total);
     scan_apply_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, n_dev, tmp);

@@ -102,8 +102,9 @@ class FicError(RuntimeError):
     def __init__(self, status, what=""):
         self.status = status
         detail = ""
-        if status in (FIC_ECUDA, FIC_ENOMEM):
-            detail = " [" + lib().fic_last_error().decode() + "]"
+        if status in (FIC_ECUDA, FIC_ENOMEM, FIC_EINVAL):
+            text = lib().fic_last_error().decode()
+            detail = " [" + text + "]" if text else ""
         super().__init__(f"{what}: {strerror(status)} ({status}){detail}")
 
 

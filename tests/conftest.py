@@ -8,9 +8,19 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
+def pytest_addoption(parser):
+    parser.addoption("--oracle-lib", default=None,
+                     help="path of another build of oracle/fic_oracle.c to check the pins "
+                          "against (the pins' mutation test)")
+
+
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: takes more than a few seconds on CPU")
+    path = config.getoption("--oracle-lib")
+    if path:
+        import oracle
+        oracle.use_library(path)
 
 
 def pytest_collection_modifyitems(config, items):

@@ -149,3 +149,76 @@ def test_wait_selftest_host_checks(fic):
         has_dev = False
     if not has_dev:
         assert f.fic_wait_selftest(False, 1000) == f.FIC_ENODEV
+
+
+SS4 = SS3 + [(10, [5, 9])]
+
+
+def _no_device():
+    try:
+        import torch
+        return not torch.cuda.is_available()
+    except Exception:
+        return True
+
+
+@pytest.mark.parametrize("case", [
+    # full pool at L = 1: (8192 - 8 + 1)^2 = 66,977,025 domains at the 4x4 step
+    dict(N=8192, B_min=4, thr=-1.0, pool_dn=0, ssets=SS3, what="argmin key"),
+    # just past the key's 2^25 columns: (5808 - 7)^2 = 33,651,601 domains
+    dict(N=5808, B_min=4, thr=-1.0, pool_dn=0, ssets=SS3, what="argmin key"),
+    # threshold pool: (4112 - 7)^2 = 16,851,025 positions to compact > 4096 x 4096
+    dict(N=4112, B_min=4, thr=4.0, pool_dn=0, ssets=SS3, what="scan limit"),
+    # top-DN pool lists its positions through the same scan
+    dict(N=4112, B_min=4, thr=-1.0, pool_dn=64, ssets=SS3, what="scan limit"),
+])
+def test_pool_sizes_beyond_the_device_limits_rejected_on_host(fic, case):
+    """Pool indices occupy 25 bits of the packed argmin key and the
+    device-wide scan takes at most 4096 tiles of 4096 elements: a step whose
+    pool or position count exceeds either is refused before any device
+    work, with the limit named, instead of a wrapped key or a failed scan."""
+    N = case["N"]
+    img = np.zeros((N, N), np.uint8)
+    with pytest.raises(fic.FicError) as e:
+        fic.fic_encode_ex(img, N, 16, case["B_min"], 1, case["thr"], case["ssets"], 8.0,
+                          pool_dn=case["pool_dn"])
+    assert e.value.status == fic.fic.FIC_EINVAL
+    assert case["what"] in str(e.value)
+
+
+def test_record_count_beyond_the_scan_limit_rejected_on_host(fic):
+    # 16 -> 2 at N = 8208: (8208 / 2)^2 = 16,842,816 finest cells > 4096 x 4096
+    N = 8208
+    img = np.zeros((N, N), np.uint8)
+    with pytest.raises(fic.FicError) as e:
+        fic.fic_encode_ex(img, N, 16, 2, 64, -1.0, SS4, 8.0)
+    assert e.value.status == fic.fic.FIC_EINVAL and "scan limit" in str(e.value)
+
+
+def test_domain_pool_beyond_the_scan_limit_rejected_on_host(fic):
+    img = np.zeros((4112, 4112), np.uint8)
+    with pytest.raises(fic.FicError) as e:
+        fic.fic_domain_pool(img, 4112, 4, 1, 4.0)
+    assert e.value.status == fic.fic.FIC_EINVAL and "scan limit" in str(e.value)
+
+
+@pytest.mark.skipif(not _no_device(), reason="would run the encode on the device")
+def test_largest_sizes_within_the_limits_pass_validation(fic):
+    """At the limits themselves validation passes; without an sm_103 device
+    the call then ends with FIC_ENODEV, not FIC_EINVAL."""
+    for N, thr in ((5792, -1.0), (4096, 4.0)):   # (5792-7)^2 full pool; (4096-7)^2 positions
+        img = np.zeros((N, N), np.uint8)
+        with pytest.raises(fic.FicError) as e:
+            fic.fic_encode_ex(img, N, 16, 4, 1, thr, SS3, 8.0)
+        assert e.value.status == fic.fic.FIC_ENODEV, N
+
+
+def test_noalloc_side_above_65535_rejected_on_host(fic):
+    # pool coordinates are packed x | y << 16: a side of 65536 is refused
+    # before the buffers are looked at (the array's pages are never touched)
+    N = 65536
+    img = np.zeros((N, N), np.uint8)
+    xy = np.zeros(16, np.int32)
+    with pytest.raises(fic.FicError) as e:
+        fic.fic.fic_domain_pool_noalloc(img, N, 16, 128, -1.0, xy)
+    assert e.value.status == fic.fic.FIC_EINVAL

@@ -3,8 +3,8 @@
 Each mutant is a copy of oracle/fic_oracle.c with one planted mistake (a
 dropped term, a wrong sign, a swapped index or order, an off-by-one, a
 wrong rounding), compiled on the CPU into a temporary library; the pin
-suite (tests/test_oracle_pins.py) then runs against it through
-FIC_ORACLE_LIB and must fail.  A control copy with no change must pass, so
+suite (tests/test_oracle_pins.py) then runs against it, named by the
+explicit --oracle-lib option of the pytest process, and must fail.  A control copy with no change must pass, so
 a failure means the mistake was seen and not that the harness broke.
 Nothing here touches the CUDA path."""
 from __future__ import annotations
@@ -100,9 +100,9 @@ def _build(src_text, d, name):
 
 
 def _pins(so):
-    env = dict(os.environ, FIC_ORACLE_LIB=so, OMP_NUM_THREADS="2")
+    env = dict(os.environ, OMP_NUM_THREADS="2")
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        "--oracle-lib", so, os.path.join(ROOT, "tests", "test_oracle_pins.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     return r.returncode, r.stdout[-2000:]
 

@@ -65,3 +65,12 @@ def test_noalloc_rejects_oversize_and_small_output(pkg):
     with pytest.raises(f.FicError) as e:
         f.fic_domain_pool_noalloc(img, 256, 8, 2, -1.0, out)
     assert e.value.status == f.FIC_ECAP
+    # pool positions are packed x | y << 16: a side above 65535 is refused
+    # even when its position count fits the scratch
+    del big
+    huge = torch.zeros((65536, 65536), dtype=torch.uint8, device="cuda")
+    with pytest.raises(f.FicError) as e:
+        f.fic_domain_pool_noalloc(huge, 65536, 16, 128, -1.0, out)
+    assert e.value.status == f.FIC_EINVAL
+    del huge
+    torch.cuda.empty_cache()
