@@ -79,6 +79,37 @@ def measured_traffic():
         return None
 
 
+def load_peaks():
+    """The driver's measured peaks (MEASURED_PEAKS.json: HBM copy GB/s, bf16
+    GEMM TFLOP/s), or {} when absent."""
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def fp16_peak(peaks):
+    """Dense FP16 tensor peak (TFLOP/s) for the contraction, which runs
+    tcgen05 kind::f16 on FP16 operands: the larger of the FP16 GEMM burst
+    measured on the GB300s (profiles/peak_gemm_fp16_bf16.json,
+    written by ``bench.py --workload peaks``) and the driver's bf16 burst
+    (fp16 and bf16 have the same nominal dense rate), so that the fraction is
+    never flattered by a low measurement; else the recipe's fallback."""
+    cands, notes = [], []
+    try:
+        pk = json.load(open(os.path.join(ROOT, "profiles", "peak_gemm_fp16_bf16.json")))
+        cands.append(float(pk["fp16"]["burst_tflops"]))
+        notes.append(f"fp16 GEMM burst {cands[-1]:.1f} (profiles/peak_gemm_fp16_bf16.json)")
+    except Exception:
+        pass
+    if "bf16_tflops" in peaks:
+        cands.append(float(peaks["bf16_tflops"]))
+        notes.append(f"bf16 GEMM burst {cands[-1]:.1f} (MEASURED_PEAKS.json, fp16 nominal equal)")
+    if not cands:
+        return 1900.0, "of fallback: 1.9 PFLOP/s bf16 burst (fp16 nominal equal)"
+    return max(cands), "of measured: max of " + "; ".join(notes)
+
+
 # ---------------------------------------------------------------- clocks
 def smi_device_id(dev):
     """The nvidia-smi --id of torch device `dev`.  torch numbers the devices
@@ -361,12 +392,18 @@ def run_gpu(args):
         stats = pkg.fic_stats_read()
         return ms, matches, stats, r, wall
 
-    # tensor-core engine (the headline), clocks sampled during the timed steps
+    # tensor-core engine (the headline): the production path as a user runs it
+    # (no per-stage events), clocks sampled during the timed steps
     sampler = ClockSampler(smi_device_id(dev))
     sampler.start()
-    ms_t, m_t, st_t, r_t, wall_t = timed(pkg.ENGINE_TENSOR, args.steps, args.warmup, True, sampler)
+    ms_t, m_t, st_u, r_t, wall_t = timed(pkg.ENGINE_TENSOR, args.steps, args.warmup, False,
+                                         sampler)
     clocks = sampler.stop()
     codes_t = dcodes[: r_t.n_codes * 16].cpu().numpy().copy()
+    # the same steps again with the library's per-stage CUDA events on the
+    # launching stream: kernel times for the roofline and the stage rates
+    ms_i, _, st_t, r_i, _ = timed(pkg.ENGINE_TENSOR, args.steps, 3, True)
+    assert r_i.n_codes == r_t.n_codes
 
     # CUDA-core engine on the same workload (fewer steps; it is much slower)
     psteps = max(1, min(args.steps, 3))
@@ -377,6 +414,8 @@ def run_gpu(args):
         identical = bool(r_t.n_codes == r_p.n_codes and np.array_equal(codes_t, codes_p))
 
     # end to end through the C ABI with host buffers (H2D image, D2H records)
+    # (each call timed on its own, host clock around the synchronous call,
+    # L2 flushed before it exactly as before each device-timed step)
     e2e_m, e2e_s = 0, float("nan")
     if "e2e" in legs:
         himg = torch.from_numpy(img).pin_memory()
@@ -385,13 +424,16 @@ def run_gpu(args):
             enc(pkg.ENGINE_TENSOR, src=himg, out=hcodes)
         torch.cuda.synchronize()
         barrier()
-        t0 = time.perf_counter()
+        e2e_s = 0.0
         for _ in range(args.steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
             r = enc(pkg.ENGINE_TENSOR, src=himg, out=hcodes)
+            e2e_s += time.perf_counter() - t0
             e2e_m += r.total_matches
         torch.cuda.synchronize()
         barrier()
-        e2e_s = time.perf_counter() - t0
 
     # max over ranks of the times; sum of work
     if world > 1:
@@ -408,12 +450,8 @@ def run_gpu(args):
     ms_per_img = ms_t / args.steps
 
     # roofline of the dominant kernel (the fused contraction + scoring)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    peak_tf = peaks.get("bf16_tflops", 1900.0)
+    peaks = load_peaks()
+    peak_tf, peak_note = fp16_peak(peaks)
     tc = st_t["contract_tc"]
     achieved = tc["flops"] / (tc["ms"] / 1e3) / 1e12 if tc["ms"] > 0 else None
     kern_ms = {k: v["ms"] / args.steps for k, v in st_t.items() if isinstance(v, dict)}
@@ -427,7 +465,7 @@ def run_gpu(args):
             stages[k] = {"ms_per_step": v["ms"] / args.steps,
                          "bytes_per_step": v["bytes"] / args.steps,
                          "GB/s": gbs, "frac_of_hbm": gbs / hbm}
-    launches = sum(v["launches"] for k, v in st_t.items() if isinstance(v, dict))
+    launches = sum(v["launches"] for k, v in st_u.items() if isinstance(v, dict))
 
     cpu = None
     if "cpu" in legs and not args.only_side:
@@ -451,6 +489,18 @@ def run_gpu(args):
                "sample": "; ".join(descs) + f"; rates weighted by the matches per step of {how}",
                "est_ms_per_image": 1e3 * est_s}
 
+    tuned = [[t["K"], t["iso_tiles"], t["refill"], t["epi_warps"], round(t["ms"], 3)]
+             for t in pkg.fic_tune_read()]
+
+    # the batching and serving forms, after the headline's timed steps (one GPU)
+    batch_res = serving_res = None
+    if world == 1 and not args.only_side:
+        if "batch" in legs:
+            batch_res = measure_batch(max(3, min(args.steps, 5)), 2)
+        if "serving" in legs:
+            t_arr, sides, simgs = serving_images(40, 4.0)
+            serving_res = measure_serving(t_arr, sides, simgs, 4.0)
+
     line = {
         "metric": METRIC, "value": gmatch_t, "unit": "Gmatch/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_img,
@@ -473,8 +523,11 @@ def run_gpu(args):
                      "kernel": "contraction (contract_tc_kernel at 16x16, "
                                "contract_tc_iso_kernel at 8x8 and 4x4)",
                      "algorithmic_flops_per_encode": tc["flops"] / max(args.steps, 1),
-                     "peak_note": "of measured: bf16 dense burst (MEASURED_PEAKS.json); fp16 "
-                                  "dense nominal equal"},
+                     "timing": "library CUDA events around each contraction launch on the "
+                               "launching stream, over a second pass of the same steps with "
+                               "per-stage events on (ms per encode with events: "
+                               f"{ms_i / args.steps:.3f})",
+                     "peak_note": peak_note},
         "stages_hbm": {"peak_gbs": hbm, "note": "algorithmic bytes / CUDA-event time of the "
                        "stage's launches; peak = measured HBM copy bandwidth "
                        "(MEASURED_PEAKS.json)", "stages": stages},
@@ -485,8 +538,9 @@ def run_gpu(args):
         "clocks": clocks,
         "wall_s_tensor": wall_t,
         # contraction shapes the tuner kept: (K, isometry tiles, refill, epilogue warps, ms)
-        "tuned_shapes": [[t["K"], t["iso_tiles"], t["refill"], t["epi_warps"], round(t["ms"], 3)]
-                         for t in pkg.fic_tune_read()],
+        "tuned_shapes": tuned,
+        "batch64": batch_res,
+        "serving": serving_res,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -501,14 +555,41 @@ BATCH_DESC = ("batch64: 64 uint8 1/f images, seeds 100..163, side uniform over {
               "4.0 bits, S {0.1},{0.2,0.4},{0.3,0.8}, RMS tol 8")
 
 
-def run_batch(args):
+def entropy_updates(results, L=2, B_max=16):
+    """Histogram updates the entropy kernel makes for the steps that ran: per
+    row run of 32 positions one full window (4n pixels), then per further
+    position 2 x min(L, 2B) x 2B (the columns that leave and enter)."""
+    tot = 0
+    for r in results:
+        N = int(r.N)
+        for lvl in range(len(r.ranges)):
+            if int(r.ranges[lvl]) <= 0:
+                continue
+            B = B_max >> lvl
+            S = 2 * B
+            per = (N - S) // L + 1 if N >= S else 0
+            if per <= 0:
+                continue
+            runs = per * ((per + 31) // 32)
+            tot += runs * S * S + (per * per - runs) * 2 * min(L, S) * S
+    return tot
+
+
+def smem_atomic_peak(sm_mhz, n_sms=152):
+    """Nominal bound of the entropy stage: the shared-memory pipe serves one
+    32-lane access per clock per SM, and a histogram update (atomic
+    increment) needs at least one."""
+    return n_sms * 32 * (sm_mhz or 2070.0) * 1e6
+
+
+def measure_batch(steps, warmup, one_by_one_steps=0, sampler_dev=None):
     """The 64-image batching workload: every image in one fic_encode_batch
-    call (one grouped contraction launch per quadtree step), against the same
-    images encoded one call at a time."""
+    call (one grouped contraction launch per quadtree step, the whole call
+    one CUDA graph from the second call on); optionally against the same
+    images encoded one call at a time.  Returns the measurement dict."""
     import torch
     import paper_1502_00324_gb300 as pkg
 
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
     imgs = fic_synth.batch_images(64)
@@ -546,26 +627,25 @@ def run_batch(args):
 
     sampler = ClockSampler(smi_device_id(dev))
     sampler.start()
-    ms_b, out_b, st_b = timed(batch, args.steps, args.warmup, True, sampler)
+    ms_b, out_b, st_u = timed(batch, steps, warmup, False, sampler)
     clocks = sampler.stop()
-    ms_s, out_s, _ = timed(one_by_one, max(1, min(args.steps, 3)), 1)
-    identical = all(np.array_equal(a.codes, b.codes) for a, b in zip(out_b, out_s))
+    # kernel times: the same call again with per-stage events on
+    ms_e, _, st_b = timed(batch, steps, 2, True)
     matches = sum(r.total_matches for r in out_b)
     med_b = statistics.median(ms_b)
-    med_s = statistics.median(ms_s)
-    launches = sum(v["launches"] for v in st_b.values() if isinstance(v, dict))
+    launches = sum(v["launches"] for v in st_u.values() if isinstance(v, dict))
     tc = st_b["contract_tc"]
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    peak_tf = peaks.get("bf16_tflops", 1900.0)
+    peak_tf, peak_note = fp16_peak(load_peaks())
     achieved = tc["flops"] / (tc["ms"] / 1e3) / 1e12 if tc["ms"] > 0 else None
-    line = {
+    kern_ms = {k: v["ms"] / steps for k, v in st_b.items() if isinstance(v, dict)}
+    upd = entropy_updates(out_b)
+    ent_ms = kern_ms.get("entropy", 0.0)
+    ent_rate = upd / (ent_ms / 1e3) if ent_ms > 0 else None
+    ent_peak = smem_atomic_peak(clocks.get("sm_mhz"))
+    res = {
         "metric": "aggregate Gmatch/s and ms per image, 64-image batch", "workload": "batch64",
         "value": matches / (med_b / 1e3) / 1e9, "unit": "Gmatch/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": med_b,
+        "steps": steps, "warmup": warmup, "ms_per_step": med_b,
         "higher_is_better": True, "dtype": "fp16->fp32 (exact int)", "data": "synthetic",
         "config": {"workload": BATCH_DESC, "images": len(imgs),
                    "sides": sorted(int(i.shape[0]) for i in imgs),
@@ -573,24 +653,43 @@ def run_batch(args):
                    "timed": "device-resident images -> host records (D2H of records inside)"},
         "ms_per_image": med_b / len(imgs), "images_per_s": len(imgs) / (med_b / 1e3),
         "matches_per_batch": matches,
-        "one_call_per_image": {"ms_per_batch": med_s,
-                               "value": matches / (med_s / 1e3) / 1e9, "unit": "Gmatch/s"},
-        "batch_over_one_by_one": med_s / med_b,
-        "codes_identical_batch_vs_single": identical,
-        "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in st_b.items()
-                               if isinstance(v, dict)},
-        "contraction_tflops": achieved, "contraction_frac_of_bf16_peak":
-            (achieved / peak_tf) if achieved else None,
-        "gpu_launches": int(launches / args.steps), "clocks": clocks,
+        "kernel_ms_per_step": kern_ms,
+        "ms_per_step_with_stage_events": statistics.median(ms_e),
+        "contraction_tflops": achieved, "contraction_frac_of_fp16_peak":
+            (achieved / peak_tf) if achieved else None, "peak_note": peak_note,
+        "entropy": {"updates_per_batch": upd, "ms_per_batch": ent_ms,
+                    "updates_per_s": ent_rate, "bound": "alu",
+                    "peak_updates_per_s": ent_peak,
+                    "frac": (ent_rate / ent_peak) if ent_rate else None,
+                    "peak_note": "nominal: 152 SMs x one 32-lane shared-memory access per "
+                                 "clock (an atomic histogram update needs at least one) x "
+                                 "the median SM clock sampled"},
+        "gpu_launches": int(launches / steps), "clocks": clocks,
     }
-    print(json.dumps(line), flush=True)
+    if one_by_one_steps:
+        ms_s, out_s, _ = timed(one_by_one, one_by_one_steps, 1)
+        med_s = statistics.median(ms_s)
+        res["one_call_per_image"] = {"ms_per_batch": med_s,
+                                     "value": matches / (med_s / 1e3) / 1e9, "unit": "Gmatch/s"}
+        res["batch_over_one_by_one"] = med_s / med_b
+        res["codes_identical_batch_vs_single"] = all(
+            np.array_equal(a.codes, b.codes) for a, b in zip(out_b, out_s))
+    return res
+
+
+def run_batch(args):
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    res = measure_batch(args.steps, args.warmup, one_by_one_steps=max(1, min(args.steps, 3)))
+    print(json.dumps(res), flush=True)
     return 0
 
 
 # ---------------------------------------------------------------- serving form
-SERVING_DESC = ("serving: Poisson arrivals (seed 7, mean 200 images/s) of uint8 1/f images "
-                "(alpha 2, seed 700000 + i), side uniform over {256, 512, 1024, 2048}; quadtree "
-                "16->8->4, L=2, entropy > 4.0 bits, S {0.1},{0.2,0.4},{0.3,0.8}, RMS tol 8")
+def serving_desc(rate_hz):
+    return (f"serving: Poisson arrivals (seed 7, mean {rate_hz:g} images/s) of uint8 1/f images "
+            "(alpha 2, seed 700000 + i), side uniform over {256, 512, 1024, 2048}; quadtree "
+            "16->8->4, L=2, entropy > 4.0 bits, S {0.1},{0.2,0.4},{0.3,0.8}, RMS tol 8")
 
 
 def _serving_image(args):
@@ -598,27 +697,36 @@ def _serving_image(args):
     return fic_synth.one_over_f(int(side), int(seed), 2.0)
 
 
-def run_serving(args):
-    """Request loop: a feeder thread submits each image at its Poisson arrival
-    time to one fic_server (host images); the main thread polls.  Latency =
-    records on the host - submit, on the server's clock."""
+def serving_images(requests, rate_hz):
+    """Arrival times, sides and images of the request stream, generated in
+    spawned workers (safe after the parent has used the GPU)."""
     import multiprocessing as mp
-    t_arr, sides = fic_synth.poisson_requests(args.requests, seed=7, mean_rate_hz=200.0)
+    t_arr, sides = fic_synth.poisson_requests(requests, seed=7, mean_rate_hz=rate_hz)
     jobs = [(int(n), 7 * 100000 + i) for i, n in enumerate(sides)]
-    # images are generated before any GPU work, in spawned workers
     with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
         imgs = pool.map(_serving_image, jobs)
+    return t_arr, sides, imgs
 
+
+def measure_serving(t_arr, sides, imgs, rate_hz, policy=0):
+    """Request loop: a feeder thread submits each image at its Poisson arrival
+    time to one fic_server (host images); the main thread polls.  Latency =
+    records on the host - submit, on the server's clock.  Before the stream,
+    each side is served alone (nothing else in the server) to give the
+    service latency without queueing."""
     import torch
     import paper_1502_00324_gb300 as pkg
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     dev = torch.device("cuda", torch.cuda.current_device())
     ss = pkg.paper_ssets(16, 4)
-    # warm-up: one image of each side through a throw-away server
+    # warm-up, then the service latency of each side alone (second pass)
+    alone = {}
     with pkg.Server(16, 4, 2, 4.0, ss, 8.0) as w:
-        for side in sorted(set(int(n) for n in sides)):
-            w.poll(w.submit(fic_synth.one_over_f(side, 1, 2.0)))
-    srv = pkg.Server(16, 4, 2, 4.0, ss, 8.0, policy=args.policy)
+        for rep in range(2):
+            for side in sorted(set(int(n) for n in sides)):
+                _, tm = w.poll(w.submit(fic_synth.one_over_f(side, 1, 2.0)))
+                if rep == 1:
+                    alone[str(side)] = tm["done_ms"] - tm["submit_ms"]
+    srv = pkg.Server(16, 4, 2, 4.0, ss, 8.0, policy=policy)
     tickets = [None] * len(imgs)
     sampler = ClockSampler(smi_device_id(dev))
     sampler.start()
@@ -652,27 +760,36 @@ def run_serving(args):
     by_side = {}
     for (enc, tm), n in zip(results, sides):
         by_side.setdefault(int(n), []).append(tm["done_ms"] - tm["submit_ms"])
-    line = {
+    offered = len(results) / max(float(t_arr[-1]), 1e-9)
+    return {
         "metric": "p50/p99 encode latency and images/s under a Poisson request stream",
         "workload": "serving", "value": len(results) / (span_ms / 1e3), "unit": "images/s",
         "n_gpus": 1, "requests": len(results), "higher_is_better": True,
         "dtype": "fp16->fp32 (exact int)", "data": "synthetic",
-        "config": {"workload": SERVING_DESC, "arrival_span_s": float(t_arr[-1]),
+        "config": {"workload": serving_desc(rate_hz), "arrival_span_s": float(t_arr[-1]),
                    "sides": {str(k): len(v) for k, v in sorted(by_side.items())},
                    "server": {"hbm_budget": st["hbm_budget"], "max_inflight": 64,
-                              "policy": ["fifo", "smallest first, 2 s aging"][args.policy]}},
+                              "policy": ["fifo", "smallest first, 2 s aging"][policy]}},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
                        "p99": float(np.percentile(lat, 99)), "max": float(lat.max()),
                        "mean_queue_wait": float(wait.mean())},
         "latency_ms_by_side_p50": {str(k): float(np.percentile(v, 50))
                                    for k, v in sorted(by_side.items())},
+        "service_ms_alone_by_side": alone,
         "gmatch_per_s": matches / (span_ms / 1e3) / 1e9,
         "server": {k: st[k] for k in ("iterations", "contraction_launches", "mean_inflight",
                                       "peak_inflight", "hbm_peak", "busy_ms", "failed")},
-        "offered_load_images_per_s": len(results) / max(float(t_arr[-1]), 1e-9),
+        "offered_load_images_per_s": offered,
+        "busy_fraction": st["busy_ms"] / max(span_ms, 1e-9),
         "wall_s": wall, "clocks": clocks,
     }
-    print(json.dumps(line), flush=True)
+
+
+def run_serving(args):
+    t_arr, sides, imgs = serving_images(args.requests, args.rate)
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    print(json.dumps(measure_serving(t_arr, sides, imgs, args.rate, args.policy)), flush=True)
     return 0
 
 
@@ -802,19 +919,88 @@ def run_compare(args):
     return 0
 
 
+def run_peaks(args):
+    """Dense GEMM peaks of this GPU through cuBLAS (torch.matmul, 8192^3,
+    FP32 accumulation): FP16 and BF16, as a burst (50 back-to-back GEMMs
+    after warm-up) and sustained (a loop of about 8 s, median of 0.5 s
+    windows after the first 2 s), CUDA events on the launching stream, with
+    the SM clocks sampled during each."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    torch.backends.cuda.matmul.allow_fp16_reduced_precision_reduction = False
+    torch.backends.cuda.matmul.allow_bf16_reduced_precision_reduction = False
+    n = 8192
+    flop = 2.0 * n * n * n
+    out = {}
+    for name, dt in (("fp16", torch.float16), ("bf16", torch.bfloat16)):
+        g = torch.Generator(device=dev).manual_seed(5)
+        a = torch.randn(n, n, device=dev, dtype=dt, generator=g)
+        b = torch.randn(n, n, device=dev, dtype=dt, generator=g)
+        c = torch.empty(n, n, device=dev, dtype=dt)
+        for _ in range(20):
+            torch.matmul(a, b, out=c)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(smi_device_id(dev))
+        sampler.start()
+        time.sleep(0.2)
+        sampler.begin()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(50):
+            torch.matmul(a, b, out=c)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sampler.end()
+        burst = 50 * flop / (e0.elapsed_time(e1) / 1e3) / 1e12
+        clk_burst = sampler.stop()
+        sampler = ClockSampler(smi_device_id(dev))
+        sampler.start()
+        time.sleep(0.2)
+        sampler.begin()
+        wins, t_end = [], time.perf_counter() + 8.0
+        while time.perf_counter() < t_end:
+            w0 = torch.cuda.Event(enable_timing=True)
+            w1 = torch.cuda.Event(enable_timing=True)
+            w0.record(stream)
+            for _ in range(200):
+                torch.matmul(a, b, out=c)
+            w1.record(stream)
+            w1.synchronize()
+            wins.append(200 * flop / (w0.elapsed_time(w1) / 1e3) / 1e12)
+        sampler.end()
+        clk_sus = sampler.stop()
+        keep = wins[max(1, len(wins) // 4):]
+        out[name] = {"burst_tflops": burst, "sustained_tflops": statistics.median(keep),
+                     "sustained_windows": len(keep), "clocks_burst": clk_burst,
+                     "clocks_sustained": clk_sus}
+        del a, b, c
+        torch.cuda.empty_cache()
+    line = {"metric": "dense GEMM TFLOP/s (cuBLAS through torch.matmul, 8192^3, fp32 accumulate)",
+            "workload": "peaks", "unit": "TFLOP/s", "n_gpus": 1, "higher_is_better": True,
+            "device": torch.cuda.get_device_name(dev), "fp16_over_bf16_burst":
+                out["fp16"]["burst_tflops"] / out["bf16"]["burst_tflops"], **out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--legs", default="tensor,plain,e2e,cpu",
+    ap.add_argument("--legs", default="tensor,plain,e2e,cpu,batch,serving",
                     help="measurements to run (profiling runs use 'tensor' alone)")
     ap.add_argument("--workload", default="precision512",
-                    choices=["precision512", "batch64", "serving", "compare", "graph"],
+                    choices=["precision512", "batch64", "serving", "compare", "graph", "peaks"],
                     help="precision512: the headline line; batch64: the 64-image batching "
                          "form; serving: the request server under a Poisson stream")
     ap.add_argument("--requests", type=int, default=200, help="serving: number of requests")
+    ap.add_argument("--rate", type=float, default=200.0,
+                    help="serving: mean arrival rate of the Poisson stream (images/s)")
     ap.add_argument("--policy", type=int, default=0, choices=[0, 1],
                     help="serving: admission order (0 FIFO, 1 smallest image first with aging)")
     ap.add_argument("--tune-mode", type=int, default=1,
@@ -835,6 +1021,8 @@ def main():
         return run_compare(args)
     if args.workload == "graph":
         return run_graph(args)
+    if args.workload == "peaks":
+        return run_peaks(args)
     return run_gpu(args)
 
 

@@ -173,3 +173,43 @@ def test_smallest_first_policy_with_aging(pkg):
     with pytest.raises(pkg.FicError) as e:
         make_server(pkg, policy=7)
     assert e.value.status == pkg.fic.FIC_EINVAL
+
+
+def test_mix_with_1024_and_2048_images_equals_alone(pkg):
+    """The serving workload's large sides: a 1024 x 1024 and a 2048 x 2048
+    request arrive among smaller ones while others are on the GPU.  Each
+    result equals the image's encode alone; the 2048 x 2048 result is also
+    checked against the oracle by a stratified sample of its leaves and
+    split parents at every step (the whole oracle encode of that image is
+    too slow for a test)."""
+    import torch
+    from tests.sampled import check_sampled
+    sides = (256, 1024, 64, 2048, 512, 128, 256, 64)
+    imgs = [fic_synth.one_over_f(n, 7100 + i, 2.0) for i, n in enumerate(sides)]
+    want = [alone(pkg, im) for im in imgs]
+    srv = make_server(pkg)
+    tickets = [None] * len(imgs)
+
+    def feed():
+        for i, im in enumerate(imgs):
+            src = torch.from_numpy(im).cuda() if i % 2 else im
+            tickets[i] = srv.submit(src)
+            time.sleep(0.003)
+
+    th = threading.Thread(target=feed)
+    th.start()
+    th.join()
+    got = {}
+    for i, t in enumerate(tickets):
+        enc, tm = srv.poll(t, wait_ms=-1)
+        np.testing.assert_array_equal(enc.codes, want[i].codes, err_msg=f"request {i}")
+        assert enc.pool_size == want[i].pool_size and enc.ranges == want[i].ranges
+        got[i] = enc
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(imgs) and st["failed"] == 0
+    i = sides.index(2048)
+    ss = pkg.paper_ssets(ARGS["B_max"], ARGS["B_min"])
+    n = check_sampled(imgs[i], got[i].codes, got[i].pool_size, ARGS["B_max"], ARGS["B_min"],
+                      ARGS["L"], ARGS["entropy_thresh"], ss, ARGS["err_tol"], "2048 request")
+    assert n >= 64 * 2

@@ -65,3 +65,32 @@ def test_batch64_images_match_the_oracle_encodes(pkg, engine):
         dg = field_digests(gpu_to_common(enc.codes, gw["B_max"]))
         bad = [f for f in dg if dg[f] != g["field_sha256"][f]]
         assert not bad, f"{what}: record fields differ from the oracle's encode: {bad}"
+
+
+def test_batch64_remaining_images_sampled_oracle(pkg):
+    """The images of the 64-image workload whose whole oracle encode is not
+    stored (the larger sides, which reach the large-pool and many-chunk
+    paths), from the same one-call batch the benchmark times: every image's
+    records tile it in the stored order, every step's pool equals the
+    oracle's, and a stratified sample of at least 64 leaves per step (image
+    border, the end of the pool, the rest at random) plus 16 split parents
+    per step are re-searched by the oracle one by one."""
+    import torch
+    from tests.sampled import check_sampled
+    gold = json.load(open(GOLD))
+    gw = gold["workload"]
+    stored = {g["index"] for g in gold["images"]}
+    imgs = fic_synth.batch_images(gw["count"], gw["seed0"])
+    ss = pkg.paper_ssets(gw["B_max"], gw["B_min"])
+    dimgs = [torch.from_numpy(im).cuda() for im in imgs]
+    got = pkg.fic_encode_batch(dimgs, gw["B_max"], gw["B_min"], gw["L"], gw["entropy_thresh"],
+                               ss, gw["err_tol"], stream=torch.cuda.current_stream())
+    rest = [i for i in range(len(imgs)) if i not in stored]
+    assert rest, "every image has a stored encode"
+    total = 0
+    for i in rest:
+        enc = got[i]
+        total += check_sampled(imgs[i], enc.codes, enc.pool_size, gw["B_max"], gw["B_min"],
+                               gw["L"], gw["entropy_thresh"], ss, gw["err_tol"],
+                               f"image {i} (N={imgs[i].shape[0]})", seed=i)
+    assert total >= 64 * len(rest)
