@@ -986,6 +986,67 @@ def run_peaks(args):
     return 0
 
 
+RATEDIST_DESC = ("ratedist: the 512x512 precision image (1/f texture, alpha 2, seed 2, 16 step "
+                 "edges), quadtree 16->8->4->2 (the paper's four steps), L=2, top-DN pools DN in "
+                 "{64, 256}, the paper's predefined S per step ({0.1}, {0.2,0.4}, {0.3,0.8}, "
+                 "{0.5,0.9}); RMS tolerance swept over {2, 4, 6, 8, 12, 16}")
+
+
+def run_ratedist(args):
+    """Rate against distortion over the split tolerance (Sec. 4, Fig. 9):
+    per point the stored stream's size (Sec. 3.3, Fig. 7, eq. 8: records and
+    the header with the domain lists), the records alone, the compression
+    ratio and the decoded PSNR (eq. 4), with the encode time."""
+    import torch
+    import paper_1502_00324_gb300 as pkg
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    img = fic_synth.workload_image("precision512")
+    N = img.shape[0]
+    dimg = torch.from_numpy(img).to(dev)
+    ss = [pkg.PAPER_S[b] for b in (16, 8, 4, 2)]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    rows = []
+    for dn in (64, 256):
+        for tol in (2.0, 4.0, 6.0, 8.0, 12.0, 16.0):
+            def enc():
+                return pkg.fic_encode_ex(dimg, N, 16, 2, 2, -1.0, ss, tol, stream=stream,
+                                         pool_dn=dn)
+            for _ in range(max(args.warmup, 1)):
+                enc()
+            ms = []
+            for _ in range(max(args.steps, 1)):
+                flush.fill_(1)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                r = enc()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            rec, iters = pkg.fic_decode(r, iters_max=64)
+            mse = float(np.mean((rec.astype(np.float64) - img) ** 2))
+            packed, rec_bits = pkg.fic_pack(dimg, r, 16, 2, 2, -1.0, ss, tol, pool_dn=dn,
+                                            stream=stream)
+            rows.append({"pool": dn, "tol": tol, "records": r.n_codes,
+                         "records_per_step": [int((r.codes["level"] == lv).sum())
+                                              for lv in range(4)],
+                         "stream_bytes": len(packed), "record_bits": rec_bits,
+                         "bpp": 8.0 * len(packed) / (N * N),
+                         "bpp_records_only": rec_bits / (N * N),
+                         "compression_ratio": N * N / len(packed),
+                         "compression_ratio_records_only": N * N * 8 / rec_bits,
+                         "psnr_db": 10 * np.log10(255.0 ** 2 / mse) if mse > 0 else None,
+                         "decode_passes": iters, "encode_ms": statistics.median(ms)})
+    line = {"metric": "bits per pixel and decoded PSNR over the RMS split tolerance",
+            "workload": "ratedist", "unit": "bpp / dB", "higher_is_better": None, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "dtype": "fp16->fp32 (exact int)",
+            "data": "synthetic", "config": {"workload": RATEDIST_DESC}, "rows": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -995,7 +1056,8 @@ def main():
     ap.add_argument("--legs", default="tensor,plain,e2e,cpu,batch,serving",
                     help="measurements to run (profiling runs use 'tensor' alone)")
     ap.add_argument("--workload", default="precision512",
-                    choices=["precision512", "batch64", "serving", "compare", "graph", "peaks"],
+                    choices=["precision512", "batch64", "serving", "compare", "graph", "peaks",
+                             "ratedist"],
                     help="precision512: the headline line; batch64: the 64-image batching "
                          "form; serving: the request server under a Poisson stream")
     ap.add_argument("--requests", type=int, default=200, help="serving: number of requests")
@@ -1023,6 +1085,8 @@ def main():
         return run_graph(args)
     if args.workload == "peaks":
         return run_peaks(args)
+    if args.workload == "ratedist":
+        return run_ratedist(args)
     return run_gpu(args)
 
 

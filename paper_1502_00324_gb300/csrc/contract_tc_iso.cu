@@ -61,11 +61,18 @@ struct IsoParams {
     int nstage, ncf;
 };
 
+__device__ __forceinline__ float fmax3(float a, float b, float c)
+{
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 template <int P, int W>
 __device__ __forceinline__ float iso_max(const float (&x)[P][W], int i)
 {
-    // balanced tree: two independent maxima, then one (shorter dependency chain)
-    if constexpr (P == 4) return fmaxf(fmaxf(x[0][i], x[1][i]), fmaxf(x[2][i], x[3][i]));
+    // two instructions for four values: one 2-input and one 3-input maximum
+    if constexpr (P == 4) return fmax3(x[0][i], x[1][i], fmaxf(x[2][i], x[3][i]));
     else return fmaxf(x[0][i], x[1][i]);
 }
 

@@ -63,73 +63,83 @@ __global__ void entropy_table_kernel(long long* T, int count)
 // One warp per run of kRun positions along x (one row of positions): the
 // 256-bin histogram of the first window in shared memory, then the window
 // slides by L: the L leftmost columns leave, L new columns enter.  Each count
-// change q -> q +- 1 changes the fixed-point sum by T[q +- 1] - T[q] (exact),
-// so per position the warp only adds its lanes' deltas.
+// change q -> q +- 1 changes the fixed-point sum by +-(T[q + 1] - T[q]) (the
+// difference table dq, exact), so a lane only adds its own deltas; its
+// running share after each position goes to shared memory, and at the end
+// of the run lane j sums the 32 shares of position j, evaluates H and
+// writes its outputs (coalesced, one FP64 evaluation per lane in parallel).
 //   thr mode (keys == NULL): flags[pos] = H > thr; near counts |H - thr| < 1e-9.
 //   top mode (keys != NULL): keys[pos] = (2^24 - 1 - Hq) << 40 | pos with
 //     Hq = floor(H 2^20 + 1/2) (larger entropy, then lower index, first), and
 //     flags[pos] = 1 when H 2^20 + 1/2 is within 1e-6 of an integer (a
 //     rounding step could move the position: counted later near the cut).
 constexpr int kRun = 32;
+constexpr int kEntWarps = 4;
+constexpr int64_t kEntMaxBlocks = 152 * 8;  // blocks loop over the runs beyond this
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(32 * kEntWarps)
 entropy_kernel(const uint8_t* __restrict__ img, int N, int B, int L, int per, double thr,
                const long long* __restrict__ T, uint32_t* __restrict__ flags,
                double* __restrict__ Hout, unsigned long long* __restrict__ keys,
                unsigned long long* __restrict__ near)
 {
-    __shared__ unsigned hist[8][256];
+    __shared__ long long dq[kEntTableCount - 1];               // T[q + 1] - T[q]
+    __shared__ unsigned hist[kEntWarps][256];
+    __shared__ long long share[kEntWarps][kRun][kRun + 1];     // [position][lane], padded
+    const int S = 2 * B, P = S * S;
+    for (int q = threadIdx.x; q < P; q += blockDim.x) dq[q] = T[q + 1] - T[q];
+    __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int runs_per_row = (per + kRun - 1) / kRun;
-    const int64_t run = (int64_t)blockIdx.x * 8 + w;
-    if (run >= (int64_t)runs_per_row * per) return;  // whole warp leaves together
-    const int iy = (int)(run / runs_per_row);
-    const int ix0 = (int)(run % runs_per_row) * kRun;
-    const int ix1 = min(per, ix0 + kRun);
-    const int S = 2 * B, P = S * S;
-    const int y = iy * L;
+    const int64_t n_runs = (int64_t)runs_per_row * per;
     unsigned* h = hist[w];
-#pragma unroll
-    for (int b = 0; b < 8; ++b) h[lane * 8 + b] = 0;
-    __syncwarp();
-    long long part = 0;  // this lane's share of sum T[q]
-    {
-        const int x = ix0 * L;
-        for (int t = lane; t < P; t += 32) {
-            const unsigned g = img[(int64_t)(y + t / S) * N + x + t % S];
-            const unsigned q = atomicAdd(&h[g], 1u);
-            part += T[q + 1] - T[q];
-        }
-    }
     const double log2P = (double)ilog2(P);
-    for (int ix = ix0; ix < ix1; ++ix) {
-        if (ix > ix0) {
-            // slide by L: columns x - L .. x - L + mc - 1 leave, x + S - mc ..
-            // x + S - 1 enter, mc = min(L, S)
-            // (L >= S: the whole window is replaced)
-            const int x = ix * L;
-            const int mc = L < S ? L : S;
-            const int m = mc * S;
-            __syncwarp();
-            for (int t = lane; t < m; t += 32) {
-                const int r = t / mc, c = t % mc;
-                const unsigned g = img[(int64_t)(y + r) * N + (x - L) + c];
-                const unsigned q = atomicSub(&h[g], 1u);
-                part += T[q - 1] - T[q];
-            }
-            __syncwarp();
-            for (int t = lane; t < m; t += 32) {
-                const int r = t / mc, c = t % mc;
-                const unsigned g = img[(int64_t)(y + r) * N + (x + S - mc) + c];
-                const unsigned q = atomicAdd(&h[g], 1u);
-                part += T[q + 1] - T[q];
+    const int mc = L < S ? L : S;  // columns that leave and enter per slide
+    const int m = mc * S;
+    for (int64_t run = (int64_t)blockIdx.x * kEntWarps + w; run < n_runs;
+         run += (int64_t)gridDim.x * kEntWarps) {
+        const int iy = (int)(run / runs_per_row);
+        const int ix0 = (int)(run % runs_per_row) * kRun;
+        const int ix1 = min(per, ix0 + kRun);
+        const int y = iy * L;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) h[lane * 8 + b] = 0;
+        __syncwarp();
+        long long part = 0;  // this lane's share of sum T[q]
+        {
+            const int x = ix0 * L;
+            for (int t = lane; t < P; t += 32) {
+                const unsigned g = img[(int64_t)(y + t / S) * N + x + t % S];
+                part += dq[atomicAdd(&h[g], 1u)];
             }
         }
-        long long tot = part;
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-        if (lane == 0) {
-            const int64_t pos = (int64_t)iy * per + ix;
+        for (int ix = ix0; ix < ix1; ++ix) {
+            if (ix > ix0) {
+                // slide by L: columns x - L .. x - L + mc - 1 leave, x + S - mc ..
+                // x + S - 1 enter (L >= S: the whole window is replaced)
+                const int x = ix * L;
+                __syncwarp();
+                for (int t = lane; t < m; t += 32) {
+                    const int r = t / mc, c = t % mc;
+                    const unsigned g = img[(int64_t)(y + r) * N + (x - L) + c];
+                    part -= dq[atomicSub(&h[g], 1u) - 1u];
+                }
+                __syncwarp();
+                for (int t = lane; t < m; t += 32) {
+                    const int r = t / mc, c = t % mc;
+                    const unsigned g = img[(int64_t)(y + r) * N + (x + S - mc) + c];
+                    part += dq[atomicAdd(&h[g], 1u)];
+                }
+            }
+            share[w][ix - ix0][lane] = part;
+        }
+        __syncwarp();
+        bool is_near = false;
+        if (ix0 + lane < ix1) {
+            long long tot = 0;
+#pragma unroll 8
+            for (int l = 0; l < 32; ++l) tot += share[w][lane][l];
+            const int64_t pos = (int64_t)iy * per + ix0 + lane;
             const double H = log2P - (double)tot / kEntScale / (double)P;
             if (Hout) Hout[pos] = H;
             if (keys) {
@@ -140,9 +150,12 @@ entropy_kernel(const uint8_t* __restrict__ img, int N, int B, int L, int per, do
                 flags[pos] = (hx - fl < 1e-6 || hx - fl > 1.0 - 1e-6) ? 1u : 0u;
             } else {
                 flags[pos] = H > thr ? 1u : 0u;
-                if (fabs(H - thr) < 1e-9) atomicAdd(near, 1ull);
+                is_near = fabs(H - thr) < 1e-9;
             }
         }
+        const unsigned nb = __ballot_sync(0xffffffffu, is_near);
+        if (lane == 0 && nb) atomicAdd(near, (unsigned long long)__popc(nb));
+        __syncwarp();  // the next run reuses this warp's histogram and shares
     }
 }
 
@@ -374,8 +387,10 @@ cudaError_t launch_entropy(const uint8_t* img, int N, int B, int L, int per, dou
     const int64_t npos = (int64_t)per * per;
     if (npos == 0) return cudaSuccess;
     const int64_t runs = (int64_t)per * ((per + kRun - 1) / kRun);
-    entropy_kernel<<<(unsigned)((runs + 7) / 8), 256, 0, s>>>(img, N, B, L, per, thr, T, flags,
-                                                                H, keys, near);
+    const int64_t blocks = (runs + kEntWarps - 1) / kEntWarps;
+    const int grid = (int)(blocks < kEntMaxBlocks ? blocks : kEntMaxBlocks);
+    entropy_kernel<<<grid, 32 * kEntWarps, 0, s>>>(img, N, B, L, per, thr, T, flags, H, keys,
+                                                   near);
     return cudaGetLastError();
 }
 

@@ -73,3 +73,19 @@ def test_stream_of_device_records_and_size_query(pkg):
     other = fic_synth.with_step_edges(128, 4, alpha=1.5)
     with pytest.raises(pkg.FicError):
         pkg.fic_pack(other, enc_h, 16, 4, 2, 4.0, ss, 8.0)
+
+
+@pytest.mark.parametrize("tol", [2.0, 16.0])
+def test_ratedist_stream_matches_oracle_at_two_tolerances(pkg, tol):
+    """The rate-distortion sweep's configuration (the 512 x 512 precision
+    image, 16 -> 2, L = 2, top-64 pools, the paper's S per step) at both ends
+    of the swept tolerance: the records, the stream bytes and the record
+    bits equal the oracle's writer on the oracle's own encode."""
+    img = fic_synth.workload_image("precision512")
+    ss = [PAPER_S[s] for s in (16, 8, 4, 2)]
+    enc = pkg.fic_encode_ex(img, 512, 16, 2, 2, -1.0, ss, tol, pool_dn=64)
+    got, pbits = pkg.fic_pack(img, enc, 16, 2, 2, -1.0, ss, tol, pool_dn=64)
+    want_codes, st = oracle.encode(img, 16, 2, 2, -1.0, ss, tol, pool_dn=64)
+    assert_same_codes(enc.codes, want_codes, 16)
+    want, wbits = oracle.pack(img, want_codes, 16, 4, 2, -1.0, ss, st["ranges"], pool_dn=64)
+    assert pbits == wbits and got == want
