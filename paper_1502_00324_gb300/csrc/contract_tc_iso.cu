@@ -449,13 +449,13 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
                 const float* cfs = reinterpret_cast<const float*>(sCF + (size_t)cidx * cf_bytes);
                 const ColExact* cis =
                     reinterpret_cast<const ColExact*>(sCF + (size_t)cidx * cf_bytes + cfc_bytes);
-#pragma unroll 1
+#pragma unroll
                 for (int pass = 0; pass < kPasses; ++pass) {
                     if (!(ok = mbar_wait(tfull(slot), tphase, err, kWaitCycles))) break;
                     tc_fence_after();
                     const uint32_t tb = tmem_base + ((uint32_t)(quad * 32) << 16) +
                                         (uint32_t)(slot * kSlotCols + hsel * kWarpCols);
-#pragma unroll 1
+#pragma unroll
                     for (int ch = 0; ch < kWarpCols / kChunk; ++ch) {
                         float x[kPass][kChunk];
                         __syncwarp();
