@@ -62,21 +62,47 @@ def config_dict(w, extra=None):
     return d
 
 
-def measured_traffic():
-    """Mean DRAM bytes per contraction launch of one encode from the committed
-    ncu capture, or None when the kernel sources changed since."""
+def contraction_profile():
+    """The committed ncu capture of the three contraction launches of one
+    encode, or None when the kernel sources changed since it was taken."""
     import hashlib
     try:
         prof = json.load(open(os.path.join(ROOT, "profiles", "contract_traffic_precision512.json")))
         h = hashlib.sha1()
         for f in prof["sources"]:
             h.update(open(os.path.join(ROOT, f), "rb").read())
-        if h.hexdigest() != prof["sources_sha1"]:
-            return None
-        ls = prof["launches"]
-        return sum(x["dram_read_bytes"] + x["dram_write_bytes"] for x in ls) / len(ls)
+        return prof if h.hexdigest() == prof["sources_sha1"] else None
     except Exception:
         return None
+
+
+def measured_traffic():
+    """Mean DRAM bytes per contraction launch of one encode from the committed
+    ncu capture, or None when the kernel sources changed since."""
+    prof = contraction_profile()
+    if prof is None:
+        return None
+    ls = prof["launches"]
+    return sum(x["dram_read_bytes"] + x["dram_write_bytes"] for x in ls) / len(ls)
+
+
+def contraction_only(flops_per_step, peak_tf):
+    """The MMA pipeline alone: the encode's algorithmic flops over the time
+    the tensor pipe was active in the committed capture (per launch,
+    duration x sm__pipe_tensor_cycles_active), against the same peak.  The
+    epilogue is not skipped (nothing is switched off in the product); the
+    counter separates the MMA's own busy time inside the fused kernels."""
+    prof = contraction_profile()
+    if prof is None or len(prof["launches"]) != len(flops_per_step):
+        return None
+    act = [x["duration_ms_under_ncu"] * x["tensor_pipe_active_pct"] / 100.0
+           for x in prof["launches"]]
+    tf = sum(flops_per_step) / (sum(act) / 1e3) / 1e12
+    return {"tflops_while_tensor_pipe_active": tf, "frac": tf / peak_tf,
+            "tensor_pipe_active_pct": [x["tensor_pipe_active_pct"] for x in prof["launches"]],
+            "fused_frac_per_step": [f / (x["duration_ms_under_ncu"] / 1e3) / 1e12 / peak_tf
+                                    for f, x in zip(flops_per_step, prof["launches"])],
+            "source": "profiles/contract_traffic_precision512.json (ncu --set full, one encode)"}
 
 
 def load_peaks():
@@ -527,7 +553,10 @@ def run_gpu(args):
                                "launching stream, over a second pass of the same steps with "
                                "per-stage events on (ms per encode with events: "
                                f"{ms_i / args.steps:.3f})",
-                     "peak_note": peak_note},
+                     "peak_note": peak_note,
+                     "contraction_only": None if args.only_side else contraction_only(
+                         [2.0 * 8 * R * D * (w["B_max"] >> l) ** 2
+                          for l, (R, D) in enumerate(zip(r_t.ranges, r_t.pool_size))], peak_tf)},
         "stages_hbm": {"peak_gbs": hbm, "note": "algorithmic bytes / CUDA-event time of the "
                        "stage's launches; peak = measured HBM copy bandwidth "
                        "(MEASURED_PEAKS.json)", "stages": stages},
@@ -680,7 +709,8 @@ def measure_batch(steps, warmup, one_by_one_steps=0, sampler_dev=None):
 def run_batch(args):
     import torch
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    res = measure_batch(args.steps, args.warmup, one_by_one_steps=max(1, min(args.steps, 3)))
+    res = measure_batch(args.steps, args.warmup,
+                        one_by_one_steps=max(1, min(args.steps, 3)) if args.single else 0)
     print(json.dumps(res), flush=True)
     return 0
 
@@ -1061,6 +1091,8 @@ def main():
                     help="precision512: the headline line; batch64: the 64-image batching "
                          "form; serving: the request server under a Poisson stream")
     ap.add_argument("--requests", type=int, default=200, help="serving: number of requests")
+    ap.add_argument("--no-single", dest="single", action="store_false",
+                    help="batch64: skip the one-call-per-image comparison")
     ap.add_argument("--rate", type=float, default=200.0,
                     help="serving: mean arrival rate of the Poisson stream (images/s)")
     ap.add_argument("--policy", type=int, default=0, choices=[0, 1],
