@@ -173,3 +173,61 @@ def test_reference_arm_weights_step_rates_by_the_encode(monkeypatch, capsys):
 def test_stored_oracle_counts_are_read():
     m = bench.oracle_encode_matches()
     assert m is not None and len(m) == 3 and all(x > 0 for x in m)
+
+
+def test_fp16_peak_is_the_larger_measured_figure(monkeypatch):
+    """The contraction's peak: the larger of the committed FP16 GEMM burst and
+    the driver's BF16 burst, so a low FP16 measurement never flatters the
+    fraction; with neither, the recipe's fallback, said so."""
+    import json
+    pk = json.load(open(os.path.join(bench.ROOT, "profiles", "peak_gemm_fp16_bf16.json")))
+    fp16 = float(pk["fp16"]["burst_tflops"])
+    v, note = bench.fp16_peak({"bf16_tflops": fp16 + 100.0})
+    assert v == fp16 + 100.0 and "MEASURED_PEAKS" in note and note.startswith("of measured")
+    v, note = bench.fp16_peak({"bf16_tflops": fp16 - 100.0})
+    assert v == fp16 and "peak_gemm_fp16_bf16" in note
+    real_open = open
+
+    def no_profile(path, *a, **k):
+        if str(path).endswith("peak_gemm_fp16_bf16.json"):
+            raise FileNotFoundError(path)
+        return real_open(path, *a, **k)
+    monkeypatch.setattr("builtins.open", no_profile)
+    v, note = bench.fp16_peak({})
+    assert v == 1900.0 and note.startswith("of fallback")
+
+
+class _Res:
+    def __init__(self, N, ranges):
+        self.N, self.ranges = N, ranges
+
+
+def test_entropy_updates_count():
+    """Per run of 32 positions one full window of (2B)^2 pixels, then
+    2 min(L, 2B) 2B updates per further position; steps no range reached
+    count nothing."""
+    # N = 64, L = 2: B = 16 -> per = (64 - 32) / 2 + 1 = 17 (one run per row)
+    r = _Res(64, [16, 0, 0])
+    assert bench.entropy_updates([r], L=2, B_max=16) == 17 * 32 * 32 + (17 * 17 - 17) * 2 * 2 * 32
+    # L = 40 >= 2B = 32 at B = 16: the whole window is replaced per position
+    r = _Res(96, [9, 4, 0])
+    per16 = (96 - 32) // 40 + 1
+    per8 = (96 - 16) // 40 + 1
+    want = per16 * 32 * 32 + (per16 * per16 - per16) * 2 * 32 * 32 + \
+        per8 * 16 * 16 + (per8 * per8 - per8) * 2 * 16 * 16
+    assert bench.entropy_updates([r], L=40, B_max=16) == want
+
+
+def test_contraction_only_uses_the_capture_while_sources_match(monkeypatch):
+    prof = bench.contraction_profile()
+    if prof is None:
+        pytest.skip("kernel sources changed since the committed capture")
+    flops = [1e12, 1e12, 1e12]
+    co = bench.contraction_only(flops, 2000.0)
+    act = sum(x["duration_ms_under_ncu"] * x["tensor_pipe_active_pct"] / 100.0
+              for x in prof["launches"])
+    assert co["tflops_while_tensor_pipe_active"] == pytest.approx(3e12 / (act / 1e3) / 1e12)
+    assert co["frac"] == pytest.approx(co["tflops_while_tensor_pipe_active"] / 2000.0)
+    assert bench.contraction_only(flops[:2], 2000.0) is None
+    monkeypatch.setattr(bench, "contraction_profile", lambda: None)
+    assert bench.contraction_only(flops, 2000.0) is None and bench.measured_traffic() is None
