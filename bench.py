@@ -10,9 +10,14 @@ device-resident records.
 
 Metric: Gmatch/s = (sum over steps of ranges x pool domains x 8 isometries)
 / encode time, for the tensor-core engine; ms per 512^2 encode, the CUDA-core
-engine's Gmatch/s and the records' equality across engines ride along.
+engine's Gmatch/s and the records' equality across engines ride along.  The
+default line also carries the roofline of the contraction (against the dense
+FP16 peak), the same encode end to end through host buffers, the oracle on a
+bounded sample (cpu_baseline), and, on one GPU, the 64-image batching
+workload and a below-capacity serving run.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py --workload batch64|serving|compare|graph|ratedist|peaks
 
 Under torchrun each rank encodes its own copy (independent replicas, weak
 scaling); rank 0 prints one JSON line.  ``--impl reference`` times the CPU
