@@ -353,7 +353,8 @@ const char* fic_strerror(int status);
  * counterpart; this is the GPU design's tile-shape choice. */
 typedef struct {
     int32_t engine, K, n_s, size_class;  /* the class                      */
-    int32_t iso_tiles;                   /* 1: isometry tiles; 0: row tiles */
+    int32_t iso_tiles;                   /* 0: row tiles; 1: isometry tiles; 2: domain-side
+                                            isometries, maximum by the TMEM load */
     int32_t refill;                      /* chunking refill cost, tiles     */
     int32_t epi_warps;                   /* epilogue warps (isometry tiles:
                                             8 with 16-column TMEM reads, or

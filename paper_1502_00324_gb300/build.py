@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfic.so")
 SOURCES = ["api.cu", "engine.cu", "graph.cu", "stages.cu", "contract_plain.cu", "contract_tc.cu", "contract_tc_iso.cu",
-           "noalloc.cu", "server.cu", "selftest.cu"]
+           "contract_tc_red.cu", "noalloc.cu", "server.cu", "selftest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]

@@ -145,6 +145,11 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
             item_coords(Q, local, chunk, mtile);
             const int ct0 = chunk * Q.per_chunk;
             const int ct1 = min(Q.n_ct, ct0 + Q.per_chunk);
+            // operand pointers in registers: the waits' memory clobbers would
+            // otherwise reload them from the problem table on every tile
+            const float* const qcf = Q.cf;
+            const __half* const qD = Q.D;
+            const int64_t qcols = Q.cols_pad;
             if (!(ok = mbar_wait_warp(a_empty, (uint32_t)((icount & 1) ^ 1), err, kWaitCycles))) break;
             if (elect_one()) {
                 mbar_expect_tx(a_full, NKB * kAKBBytes);
@@ -159,7 +164,7 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
                 if (!(ok = mbar_wait_warp(cfe(cidx), cphase ^ 1, err, kWaitCycles))) break;
                 if (elect_one()) {
                     mbar_expect_tx(cff(cidx), cf_bytes);
-                    bulk_g2s(smem_u32(sCF + (size_t)cidx * cf_bytes), Q.cf + (int64_t)ct * kN * sp.cw,
+                    bulk_g2s(smem_u32(sCF + (size_t)cidx * cf_bytes), qcf + (int64_t)ct * kN * sp.cw,
                              cf_bytes, cff(cidx));
                 }
                 __syncwarp();
@@ -173,7 +178,7 @@ contract_tc_kernel(const __grid_constant__ TcParams P, const __grid_constant__ S
                     if (elect_one()) {
                         mbar_expect_tx(full(sidx), kBStageBytes);
                         bulk_g2s(smem_u32(sB + (size_t)sidx * kBStageBytes),
-                                 Q.D + ((int64_t)kb * Q.cols_pad * KB + (int64_t)ct * kN * KB),
+                                 qD + ((int64_t)kb * qcols * KB + (int64_t)ct * kN * KB),
                                  kBStageBytes, full(sidx));
                     }
                     __syncwarp();

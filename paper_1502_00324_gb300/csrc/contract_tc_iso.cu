@@ -305,6 +305,11 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
             const int ct0 = chunk * Q.per_chunk;
             const int ct1 = min(Q.n_ct, ct0 + Q.per_chunk);
             const int64_t rpad = Q.rows_pad / 8;
+            // operand pointers in registers: the waits' memory clobbers would
+            // otherwise reload them from the problem table on every tile
+            const float* const qcf = Q.cf;
+            const ColExact* const qci = Q.ci;
+            const __half* const qD = Q.D;
             if (!(ok = mbar_wait_warp(a_empty, (uint32_t)((icount & 1) ^ 1), err, kWaitCycles))) break;
             if (elect_one()) {
                 mbar_expect_tx(a_full, 8 * kAIsoBytes);
@@ -319,10 +324,10 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
                 if (!(ok = mbar_wait_warp(cfe(cidx), cphase ^ 1, err, kWaitCycles))) break;
                 if (elect_one()) {
                     mbar_expect_tx(cff(cidx), cf_bytes);
-                    bulk_g2s(smem_u32(sCF + (size_t)cidx * cf_bytes), Q.cf + (int64_t)ct * kN * sp.cw,
+                    bulk_g2s(smem_u32(sCF + (size_t)cidx * cf_bytes), qcf + (int64_t)ct * kN * sp.cw,
                              cfc_bytes, cff(cidx));
                     bulk_g2s(smem_u32(sCF + (size_t)cidx * cf_bytes + cfc_bytes),
-                             Q.ci + (int64_t)ct * kN, cf_bytes - cfc_bytes, cff(cidx));
+                             qci + (int64_t)ct * kN, cf_bytes - cfc_bytes, cff(cidx));
                 }
                 __syncwarp();
                 ++cfi;
@@ -333,7 +338,7 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
                 if (!(ok = mbar_wait_warp(empty(sidx), sphase ^ 1, err, kWaitCycles))) break;
                 if (elect_one()) {
                     mbar_expect_tx(full(sidx), kBStageBytes);
-                    bulk_g2s(smem_u32(sB + (size_t)sidx * kBStageBytes), Q.D + (int64_t)ct * kN * K,
+                    bulk_g2s(smem_u32(sB + (size_t)sidx * kBStageBytes), qD + (int64_t)ct * kN * K,
                              kBStageBytes, full(sidx));
                 }
                 __syncwarp();
@@ -437,14 +442,15 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
             const bool valid = range < Q.R && !range_is_flat(r, sp.n);
             RowState st;
             row_state_init(st);
-            if (valid) row_state_seed(st, Q.gbest + range, inv_n, r.delta);
+            long long* const gb = Q.gbest + range;  // in a register for the whole item
+            if (valid) row_state_seed(st, gb, inv_n, r.delta);
             // the best key other chunks of this range have published, read one
             // tile ahead; this chunk publishes its own improvements per tile
-            long long gseen = valid ? __ldcg(Q.gbest + range) : kNoCandidate;
+            long long gseen = valid ? __ldcg(gb) : kNoCandidate;
             long long gpub = kNoCandidate;
             for (int ct = ct0; ct < ct1; ++ct) {
                 if (gseen < kNoCandidate) st.thr = fminf(st.thr, thr_from_h(gseen, inv_n, r.delta));
-                if (valid) gseen = __ldcg(Q.gbest + range);
+                if (valid) gseen = __ldcg(gb);
                 if (!(ok = mbar_wait(cff(cidx), cphase, err, kWaitCycles))) break;
                 const float* cfs = reinterpret_cast<const float*>(sCF + (size_t)cidx * cf_bytes);
                 const ColExact* cis =
@@ -483,7 +489,7 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
                 }
                 if (!ok) break;
                 if (st.h < gpub) {
-                    atomicMin(Q.gbest + range, st.h);
+                    atomicMin(gb, st.h);
                     gpub = st.h;
                 }
                 __syncwarp();
@@ -495,7 +501,7 @@ contract_tc_iso_kernel(const __grid_constant__ IsoParams P, const __grid_constan
             }
             if (!ok) break;
             if (valid) {
-                row_state_publish(st, Q.gbest + range);
+                row_state_publish(st, gb);
                 Best b;
                 b.h = st.h;
                 b.idx = st.idx;

@@ -165,11 +165,17 @@ std::vector<TuneChoice> tune_candidates(const fic_params& p, int lvl)
     const int K = k_pad(B * B);
     const bool iso_ok =
         p.engine == FIC_ENGINE_TENSOR && contract_tc_iso_supports(K, p.S_sets[lvl].n_s);
+    const bool red_ok =
+        p.engine == FIC_ENGINE_TENSOR && contract_tc_red_supports(B * B, p.S_sets[lvl].n_s);
     std::vector<TuneChoice> c;
     for (int refill : {1, 2, 4}) c.push_back(TuneChoice{iso_ok ? 1 : 0, refill, 0});
     if (iso_ok) {
         c.push_back(TuneChoice{1, 2, 1});  // 16 epilogue warps, 8-column reads
         c.push_back(TuneChoice{0, 2, 0});  // the row kernel on the same step
+    }
+    if (red_ok) {
+        for (int refill : {2, 4}) c.push_back(TuneChoice{2, refill, 0});
+        c.push_back(TuneChoice{2, 2, 1});  // 16 epilogue warps, batches of 4 domains
     }
     return c;
 }
@@ -655,7 +661,9 @@ int Engine::step(const fic_params& p, const std::vector<Job*>& jobs, Launcher& L
         if (p.engine == FIC_ENGINE_TENSOR) {
             FIC_TRY(cudaMemsetAsync(a.err, 0, 2 * sizeof(int), s));
             L.begin(FIC_K_CONTRACT_TC);
-            FIC_TRY(h.iso ? launch_contract_tc_iso(a, s) : launch_contract_tc(a, s));
+            FIC_TRY(h.red   ? launch_contract_tc_red(a, s)
+                    : h.iso ? launch_contract_tc_iso(a, s)
+                            : launch_contract_tc(a, s));
             L.end(1, flops, bytes, matches);
         } else {
             L.begin(FIC_K_CONTRACT_PLAIN);

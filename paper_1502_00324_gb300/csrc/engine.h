@@ -143,8 +143,9 @@ struct Job {
     fic_result res{};               // counters; codes set by finish()
 };
 
-// A contraction shape choice of the tuner: kernel family (1: isometry-in-
-// accumulator tiles where they apply, 0: row tiles), the chunking's
+// A contraction shape choice of the tuner: kernel family where it applies
+// (0: row tiles, 1: isometry-in-accumulator tiles, 2: domain-side
+// isometries with the maximum taken by the TMEM load), the chunking's
 // per-item refill cost in tiles, and the isometry kernel's epilogue (0: 8
 // warps x 16-column TMEM reads, 1: 16 warps x 8-column reads).
 struct TuneChoice {

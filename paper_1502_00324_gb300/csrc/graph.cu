@@ -508,7 +508,9 @@ int Engine::graph_build(GraphPlan& G, cudaStream_t /*s*/)
             if (p.engine == FIC_ENGINE_TENSOR) {
                 FIC_TRY(cudaMemsetAsync(a.err, 0, 2 * sizeof(int), s));
                 L.begin(FIC_K_CONTRACT_TC);
-                FIC_TRY(h.iso ? launch_contract_tc_iso(a, s) : launch_contract_tc(a, s));
+                FIC_TRY(h.red   ? launch_contract_tc_red(a, s)
+                        : h.iso ? launch_contract_tc_iso(a, s)
+                                : launch_contract_tc(a, s));
                 L.end(1);
             } else {
                 L.begin(FIC_K_CONTRACT_PLAIN);

@@ -33,6 +33,14 @@ cudaError_t launch_contract_tc_iso(const ContractArgs& a, cudaStream_t s);
 bool contract_tc_iso_supports(int K, int ns);
 int contract_tc_iso_parts_per_chunk(int variant);
 int contract_tc_iso_ntile(int K);
+// Domain-side isometry tensor kernel (n = B^2 = 4, 16 or 64, |S| <= 3): A in
+// the iso-major layout (isometry 0 block: the ranges as they are), the
+// pool operand as gathered; the eight isometries of each domain are built in
+// shared memory and their maximum comes from tcgen05.ld.red (sm_103a).
+cudaError_t launch_contract_tc_red(const ContractArgs& a, cudaStream_t s);
+bool contract_tc_red_supports(int n, int ns);
+int contract_tc_red_ntile();
+int contract_tc_red_parts_per_chunk(int variant);  // 0: 8 epilogue warps, 1: 16
 size_t contract_tc_smem_bytes(int K);
 int contract_tc_parts_per_chunk();  // partial bests per (range, column chunk)
 int contract_tc_ntile();            // pool columns per tensor-core tile

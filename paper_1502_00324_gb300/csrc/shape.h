@@ -38,7 +38,8 @@ inline StepParams make_step(const fic_sset& s, int n)
 struct StepShape {
     int B, n2, K;
     StepParams sp;
-    bool iso;            // isometry-in-accumulator tensor kernel
+    bool iso;            // iso-major range operand (isometry or domain-side kernel)
+    bool red;            // domain-side isometries, maximum by the TMEM load
     int64_t tile_w;      // pool columns per tile
     int parts_per_chunk; // partial bests per (range, column chunk)
     int refill;          // chunking: per-item refill cost in tiles
@@ -55,11 +56,15 @@ inline StepShape step_shape(const fic_params& p, int lvl, const TuneChoice& v)
     // isometry-in-accumulator kernel: ranges in TMEM lanes, one accumulator
     // per isometry (iso-major A); row kernel: rows are (range, isometry)
     const bool tc = p.engine == FIC_ENGINE_TENSOR;
-    h.iso = tc && v.iso && contract_tc_iso_supports(h.K, h.sp.ns);
-    h.tile_w = h.iso ? contract_tc_iso_ntile(h.K) : (tc ? contract_tc_ntile() : kPlainNTile);
+    h.red = tc && v.iso == 2 && contract_tc_red_supports(h.n2, h.sp.ns);
+    h.iso = h.red || (tc && v.iso == 1 && contract_tc_iso_supports(h.K, h.sp.ns));
+    h.tile_w = h.red   ? contract_tc_red_ntile()
+               : h.iso ? contract_tc_iso_ntile(h.K)
+                       : (tc ? contract_tc_ntile() : kPlainNTile);
     h.epi = v.epi;
-    h.parts_per_chunk = h.iso ? contract_tc_iso_parts_per_chunk(h.epi)
-                              : (tc ? contract_tc_parts_per_chunk() : 1);
+    h.parts_per_chunk = h.red   ? contract_tc_red_parts_per_chunk(h.epi)
+                        : h.iso ? contract_tc_iso_parts_per_chunk(h.epi)
+                                : (tc ? contract_tc_parts_per_chunk() : 1);
     h.refill = v.refill > 0 ? v.refill : 2;
     return h;
 }

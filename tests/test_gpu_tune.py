@@ -45,7 +45,7 @@ def test_every_shape_gives_the_oracle_records(pkg, case):
     want, _ = oracle.encode(img, case["B_max"], case["B_min"], case["L"], case["thr"], ss,
                             case["tol"], pool_dn=case["dn"])
     outs = []
-    for mode in (0, 2, 3, 4, 5, 6):
+    for mode in (0, 2, 3, 4, 5, 6, 7, 8, 9):
         pkg.fic_tune_mode(mode)
         enc = pkg.fic_encode_ex(img, case["N"], case["B_max"], case["B_min"], case["L"],
                                 case["thr"], ss, case["tol"], pool_dn=case["dn"])
@@ -66,7 +66,7 @@ def test_tuned_classes_are_recorded(pkg):
     table = pkg.fic_tune_read()
     assert table, "no tuned class recorded"
     for t in table:
-        assert t["candidates"] >= 3 and t["refill"] in (1, 2, 4) and t["iso_tiles"] in (0, 1)
+        assert t["candidates"] >= 3 and t["refill"] in (1, 2, 4) and t["iso_tiles"] in (0, 1, 2)
         assert t["epi_warps"] in (8, 16)
         assert t["ms"] > 0
     # a second encode of the same classes reuses the choices (no new entries)
