@@ -25,8 +25,8 @@
 // the raw pool tiles and the column constants; warp 1 owns TMEM and issues
 // tcgen05.mma / tcgen05.commit; warps 2-3 build the transformed B stages
 // (alternate tiles); warps 4-11 are the epilogue (warp w: TMEM lanes
-// 32 (w % 4) .. +31, one half of a tile's domains).  Every mbarrier wait is
-// bounded (tc_common.cuh).
+// 32 (w % 4) .. +31, the tiles of parity (w - 4) / 4 with all their
+// domains).  Every mbarrier wait is bounded (tc_common.cuh).
 #include "epilogue.cuh"
 #include "kernels.h"
 #include "tc_common.cuh"
@@ -42,18 +42,16 @@ constexpr uint32_t kTmemCols = kSlots * kTileN;
 constexpr int kXformWarps = 2;
 constexpr int kFirstEpiWarp = 2 + kXformWarps;
 
-// Epilogue decompositions (chosen by the tuner): EPI warps = 4 lane quarters
-// x EPI / 4 parts of a tile's domains, TMEM loads in batches of BATCH
-// domains.  8 warps: 16 domains per warp and tile, batches of 8; 16 warps:
-// 8 domains, batches of 4 (more warps to hide latency, fewer registers).
-template <int EPI> struct RedEpi {
-    static constexpr int kEpiWarps = EPI;
-    static constexpr int kParts = EPI / 4;
-    static constexpr int kDomPerWarp = kDom / kParts;
-    static constexpr int kBatch = EPI == 16 ? 4 : 8;
-    static constexpr int kThreads = 32 * (kFirstEpiWarp + EPI);
-    static constexpr int kMaxRegs = 65536 / kThreads / 8 * 8;
-};
+// Epilogue: 8 warps = 4 lane quarters x 2 tile parities.  Warp (q, p) takes
+// the tiles t with t % 2 == p, all 32 domains of each in batches of kBatch,
+// so the two warps of a lane quarter alternate tiles and TMEM slots (slot p)
+// and each slot is handed back by 4 warps.
+constexpr int kEpiWarps = 8;
+constexpr int kParts = 2;               // partial bests per (range, chunk): one per parity
+constexpr int kBatch = 8;               // domains per batch of TMEM loads
+constexpr int kThreads = 32 * (kFirstEpiWarp + kEpiWarps);
+constexpr int kMaxRegs = 65536 / kThreads / 8 * 8;
+static_assert(kSlots == 2 && kEpiWarps == 8, "two parities, one TMEM slot each");
 
 struct RedParams {
     const Problem* probs;
@@ -92,19 +90,6 @@ __device__ __forceinline__ void tmem_wait_batch(float (&x)[8][8], float (&mx)[8]
     asm volatile(""
                  : "+f"(mx[0]), "+f"(mx[1]), "+f"(mx[2]), "+f"(mx[3]), "+f"(mx[4]), "+f"(mx[5]),
                    "+f"(mx[6]), "+f"(mx[7]));
-}
-
-// The same for a batch of 4 domains.
-__device__ __forceinline__ void tmem_wait_batch(float (&x)[4][8], float (&mx)[4])
-{
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+f"(x[0][0]), "+f"(x[0][1]), "+f"(x[0][2]), "+f"(x[0][3]), "+f"(x[0][4]), "+f"(x[0][5]), "+f"(x[0][6]), "+f"(x[0][7]),
-                   "+f"(x[1][0]), "+f"(x[1][1]), "+f"(x[1][2]), "+f"(x[1][3]), "+f"(x[1][4]), "+f"(x[1][5]), "+f"(x[1][6]), "+f"(x[1][7]),
-                   "+f"(x[2][0]), "+f"(x[2][1]), "+f"(x[2][2]), "+f"(x[2][3]), "+f"(x[2][4]), "+f"(x[2][5]), "+f"(x[2][6]), "+f"(x[2][7]),
-                   "+f"(x[3][0]), "+f"(x[3][1]), "+f"(x[3][2]), "+f"(x[3][3]), "+f"(x[3][4]), "+f"(x[3][5]), "+f"(x[3][6]), "+f"(x[3][7]),
-                   "+f"(mx[0]), "+f"(mx[1]), "+f"(mx[2]), "+f"(mx[3])
-                 :
-                 : "memory");
 }
 
 // Makes this thread's generic-proxy shared-memory writes visible to the
@@ -298,15 +283,11 @@ struct RedLayout {
     static constexpr uint32_t kStageBytes = (uint32_t)kDom * kSboB;
 };
 
-template <int B, int NS, int EPI>
-__global__ void __maxnreg__(RedEpi<EPI>::kMaxRegs)
+template <int B, int NS>
+__global__ void __maxnreg__(kMaxRegs)
 contract_tc_red_kernel(const __grid_constant__ RedParams P, const __grid_constant__ StepParams sp)
 {
     using Lay = RedLayout<B>;
-    constexpr int kEpiWarps = RedEpi<EPI>::kEpiWarps;
-    constexpr int kParts = RedEpi<EPI>::kParts;
-    constexpr int kDomPerWarp = RedEpi<EPI>::kDomPerWarp;
-    constexpr int kBatch = RedEpi<EPI>::kBatch;
     constexpr int K = Lay::K;
     static_assert(K == 16 || K == 64, "one K-block per tile");
     constexpr int NW = Lay::NW;
@@ -353,11 +334,11 @@ contract_tc_red_kernel(const __grid_constant__ RedParams P, const __grid_constan
         }
         for (int a = 0; a < kSlots; ++a) {
             mbar_init(tfull(a), 1);
-            mbar_init(tempty(a), kEpiWarps);
+            mbar_init(tempty(a), kEpiWarps / kSlots);
         }
         for (int c = 0; c < ncf; ++c) {
             mbar_init(cff(c), 1);
-            mbar_init(cfe(c), kEpiWarps);
+            mbar_init(cfe(c), kEpiWarps / 2);  // the 4 warps of tile parity c % 2
         }
         mbar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -540,10 +521,12 @@ contract_tc_red_kernel(const __grid_constant__ RedParams P, const __grid_constan
         // ------------------------------------------------------------ epilogue
         const int e = warp - kFirstEpiWarp;
         const int quad = warp & 3;   // TMEM lanes (ranges) 32 quad .. +31
-        const int hsel = e >> 2;     // part of a tile's domains
+        const int par = e >> 2;      // this warp's tiles: t % 2 == par, TMEM slot par
         const float inv_n = 1.0f / (float)sp.n;
-        int cidx = 0, slot = 0;          // constants ring and TMEM slot positions
-        uint32_t cphase = 0, tphase = 0; // and their parities
+        int cidx = 0;                // constants ring position of tile t
+        uint32_t cphase = 0;         // and its parity
+        uint32_t tphase = 0;         // phase of this warp's TMEM slot
+        int64_t t = 0;               // tile counter of the CTA
         bool ok = true;
         for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
             const Problem& Q = P.probs[find_problem(P.probs, P.n_probs, item)];
@@ -560,61 +543,59 @@ contract_tc_red_kernel(const __grid_constant__ RedParams P, const __grid_constan
             row_state_init(st);
             long long* const gb = Q.gbest + range;  // in a register for the whole item
             if (valid) row_state_seed(st, gb, inv_n, r.delta);
-            // the best key other chunks of this range have published, read one
-            // tile ahead; this chunk publishes its own improvements per tile
+            // the best key other warps and chunks of this range have published,
+            // read one tile ahead; this warp publishes its improvements per tile
             long long gseen = valid ? __ldcg(gb) : kNoCandidate;
             long long gpub = kNoCandidate, gthr = kNoCandidate;
-            for (int ct = ct0; ct < ct1; ++ct) {
-                if (gseen < gthr) {
-                    // a better key than the one already in the threshold
-                    st.thr = fminf(st.thr, thr_from_h(gseen, inv_n, r.delta));
-                    gthr = gseen;
-                }
-                if (valid) gseen = __ldcg(gb);
-                if (!(ok = mbar_wait(cff(cidx), cphase, err, kWaitCycles))) break;
-                const float* cfs = reinterpret_cast<const float*>(sCF + (size_t)cidx * cf_bytes);
-                const ColExact* cis =
-                    reinterpret_cast<const ColExact*>(sCF + (size_t)cidx * cf_bytes + cfc_bytes);
-                if (!(ok = mbar_wait(tfull(slot), tphase, err, kWaitCycles))) break;
-                tc_fence_after();
-                const uint32_t tb = tmem_base + ((uint32_t)(quad * 32) << 16) +
-                                    (uint32_t)(slot * kTileN + hsel * kDomPerWarp * 8);
+            for (int ct = ct0; ct < ct1; ++ct, ++t) {
+                if ((int)(t & 1) == par) {
+                    if (gseen < gthr) {
+                        // a better key than the one already in the threshold
+                        st.thr = fminf(st.thr, thr_from_h(gseen, inv_n, r.delta));
+                        gthr = gseen;
+                    }
+                    if (valid) gseen = __ldcg(gb);
+                    if (!(ok = mbar_wait(cff(cidx), cphase, err, kWaitCycles))) break;
+                    const float* cfs = reinterpret_cast<const float*>(sCF + (size_t)cidx * cf_bytes);
+                    const ColExact* cis =
+                        reinterpret_cast<const ColExact*>(sCF + (size_t)cidx * cf_bytes + cfc_bytes);
+                    if (!(ok = mbar_wait(tfull(par), tphase, err, kWaitCycles))) break;
+                    tc_fence_after();
+                    const uint32_t tb = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(par * kTileN);
 #pragma unroll
-                for (int bt = 0; bt < kDomPerWarp / kBatch; ++bt) {
-                    float x[kBatch][8], mx[kBatch];
-                    __syncwarp();
-#pragma unroll
-                    for (int d = 0; d < kBatch; ++d)
-                        tmem_ldred8(tb + (uint32_t)(8 * (bt * kBatch + d)), x[d], mx[d]);
-                    // the batch's filter constants load while the TMEM reads are in flight
-                    const int g0 = (hsel * kDomPerWarp + bt * kBatch) / 4;
-                    float4 cc[kBatch / 4][1 + NS];
-                    red_consts<NS, kBatch / 4>(cfs, g0, cc);
-                    tmem_wait_batch(x, mx);
-                    if (bt == kDomPerWarp / kBatch - 1) {
-                        // the tile is in registers: hand the slot back to the MMA
-                        tc_fence_before();
+                    for (int bt = 0; bt < kDom / kBatch; ++bt) {
+                        float x[kBatch][8], mx[kBatch];
                         __syncwarp();
-                        if (lane == 0) mbar_arrive(tempty(slot));
+#pragma unroll
+                        for (int d = 0; d < kBatch; ++d)
+                            tmem_ldred8(tb + (uint32_t)(8 * (bt * kBatch + d)), x[d], mx[d]);
+                        // the batch's filter constants load while the TMEM reads are in flight
+                        const int g0 = bt * kBatch / 4;
+                        float4 cc[kBatch / 4][1 + NS];
+                        red_consts<NS, kBatch / 4>(cfs, g0, cc);
+                        tmem_wait_batch(x, mx);
+                        if (bt == kDom / kBatch - 1) {
+                            // the tile is in registers: hand the slot back to the MMA
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(tempty(par));
+                        }
+                        if (valid) {
+                            float gm[kBatch / 4];
+                            const float mn = red_pass1<NS, kBatch / 4>(mx, cc, -r.a, sp, gm);
+                            if (mn <= st.thr)
+                                red_pass2<NS, kBatch / 4>(st, x, mx, mn, gm, cfs, g0, ct * kDom,
+                                                          -r.a, r.delta, inv_n, r.sr, cis, qdn, &sp);
+                        }
                     }
-                    if (valid) {
-                        float gm[kBatch / 4];
-                        const float mn = red_pass1<NS, kBatch / 4>(mx, cc, -r.a, sp, gm);
-                        if (mn <= st.thr)
-                            red_pass2<NS, kBatch / 4>(st, x, mx, mn, gm, cfs, g0, ct * kDom, -r.a,
-                                                      r.delta, inv_n, r.sr, cis, qdn, &sp);
-                    }
-                }
-                if (++slot == kSlots) {
-                    slot = 0;
                     tphase ^= 1;
+                    if (st.h < gpub) {
+                        atomicMin(gb, st.h);
+                        gpub = st.h;
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(cfe(cidx));
                 }
-                if (st.h < gpub) {
-                    atomicMin(gb, st.h);
-                    gpub = st.h;
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(cfe(cidx));
                 if (++cidx == ncf) {
                     cidx = 0;
                     cphase ^= 1;
@@ -627,7 +608,7 @@ contract_tc_red_kernel(const __grid_constant__ RedParams P, const __grid_constan
                 b.h = st.h;
                 b.idx = st.idx;
                 b.pad = 0;
-                Q.part[(int64_t)range * (kParts * Q.n_chunks) + kParts * chunk + hsel] = b;
+                Q.part[(int64_t)range * (kParts * Q.n_chunks) + kParts * chunk + par] = b;
             }
         }
     }
@@ -651,7 +632,7 @@ size_t red_layout(int cw, int* nraw_out, int* nstage_out, int* ncf_out)
 {
     using Lay = RedLayout<B>;
     const size_t cf_tile = (size_t)kDom * cw * 4 + (size_t)kDom * sizeof(ColExact);
-    const int ncf = 16, nraw = Lay::K == 64 ? 8 : 16;
+    const int ncf = 16, nraw = Lay::K == 64 ? 8 : 16;  // ncf even: entry c serves tile parity c % 2
     const size_t fixed = Lay::kAbytes + (size_t)nraw * Lay::kRawBytes + (size_t)ncf * cf_tile + 1024;
     int ns = (int)((kSmemBudget - fixed) / Lay::kStageBytes);
     if (ns > 8) ns = 8;
@@ -663,12 +644,12 @@ size_t red_layout(int cw, int* nraw_out, int* nstage_out, int* ncf_out)
     return total < kSmemMinForOneCta ? kSmemMinForOneCta : total;
 }
 
-template <int B, int NS, int EPI>
+template <int B, int NS>
 cudaError_t launch_red_kns(const ContractArgs& a, cudaStream_t s)
 {
     int nraw = 0, nstage = 0, ncf = 0;
     const size_t smem = red_layout<B>(a.sp.cw, &nraw, &nstage, &ncf);
-    auto kern = contract_tc_red_kernel<B, NS, EPI>;
+    auto kern = contract_tc_red_kernel<B, NS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -682,25 +663,19 @@ cudaError_t launch_red_kns(const ContractArgs& a, cudaStream_t s)
     P.nstage = nstage;
     P.ncf = ncf;
     const int grid = P.n_items < a.grid_ctas ? P.n_items : a.grid_ctas;
-    kern<<<grid, RedEpi<EPI>::kThreads, smem, s>>>(P, a.sp);
+    kern<<<grid, kThreads, smem, s>>>(P, a.sp);
     return cudaGetLastError();
-}
-
-template <int B, int EPI>
-cudaError_t launch_red_be(const ContractArgs& a, cudaStream_t s)
-{
-    switch (a.sp.ns) {
-        case 1: return launch_red_kns<B, 1, EPI>(a, s);
-        case 2: return launch_red_kns<B, 2, EPI>(a, s);
-        case 3: return launch_red_kns<B, 3, EPI>(a, s);
-        default: return cudaErrorInvalidValue;  // larger S sets use the row kernel
-    }
 }
 
 template <int B>
 cudaError_t launch_red_b(const ContractArgs& a, cudaStream_t s)
 {
-    return a.variant == 1 ? launch_red_be<B, 16>(a, s) : launch_red_be<B, 8>(a, s);
+    switch (a.sp.ns) {
+        case 1: return launch_red_kns<B, 1>(a, s);
+        case 2: return launch_red_kns<B, 2>(a, s);
+        case 3: return launch_red_kns<B, 3>(a, s);
+        default: return cudaErrorInvalidValue;  // larger S sets use the row kernel
+    }
 }
 
 }  // namespace
@@ -710,10 +685,7 @@ bool contract_tc_red_supports(int n, int ns)
     return (n == 4 || n == 16 || n == 64) && ns >= 1 && ns <= 3;
 }
 int contract_tc_red_ntile() { return kDom; }
-int contract_tc_red_parts_per_chunk(int variant)
-{
-    return variant == 1 ? RedEpi<16>::kParts : RedEpi<8>::kParts;
-}
+int contract_tc_red_parts_per_chunk() { return kParts; }
 
 cudaError_t launch_contract_tc_red(const ContractArgs& a, cudaStream_t s)
 {

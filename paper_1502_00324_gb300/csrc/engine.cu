@@ -173,10 +173,8 @@ std::vector<TuneChoice> tune_candidates(const fic_params& p, int lvl)
         c.push_back(TuneChoice{1, 2, 1});  // 16 epilogue warps, 8-column reads
         c.push_back(TuneChoice{0, 2, 0});  // the row kernel on the same step
     }
-    if (red_ok) {
+    if (red_ok)
         for (int refill : {2, 4}) c.push_back(TuneChoice{2, refill, 0});
-        c.push_back(TuneChoice{2, 2, 1});  // 16 epilogue warps, batches of 4 domains
-    }
     return c;
 }
 

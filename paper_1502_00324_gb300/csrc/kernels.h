@@ -40,7 +40,7 @@ int contract_tc_iso_ntile(int K);
 cudaError_t launch_contract_tc_red(const ContractArgs& a, cudaStream_t s);
 bool contract_tc_red_supports(int n, int ns);
 int contract_tc_red_ntile();
-int contract_tc_red_parts_per_chunk(int variant);  // 0: 8 epilogue warps, 1: 16
+int contract_tc_red_parts_per_chunk();
 size_t contract_tc_smem_bytes(int K);
 int contract_tc_parts_per_chunk();  // partial bests per (range, column chunk)
 int contract_tc_ntile();            // pool columns per tensor-core tile

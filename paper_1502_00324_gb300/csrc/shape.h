@@ -62,7 +62,7 @@ inline StepShape step_shape(const fic_params& p, int lvl, const TuneChoice& v)
                : h.iso ? contract_tc_iso_ntile(h.K)
                        : (tc ? contract_tc_ntile() : kPlainNTile);
     h.epi = v.epi;
-    h.parts_per_chunk = h.red   ? contract_tc_red_parts_per_chunk(h.epi)
+    h.parts_per_chunk = h.red   ? contract_tc_red_parts_per_chunk()
                         : h.iso ? contract_tc_iso_parts_per_chunk(h.epi)
                                 : (tc ? contract_tc_parts_per_chunk() : 1);
     h.refill = v.refill > 0 ? v.refill : 2;
