@@ -204,51 +204,70 @@ __device__ __forceinline__ float red_pass1(const float (&c)[4 * G], const float4
     return mn;
 }
 
-// Exact re-scoring of the candidates of a batch whose filter is within
-// 2 delta of the batch minimum mn and under the range's threshold (ci: the
-// tile's exact column sums, cf its filter constants, both indexed by the
-// domain within the tile).  Candidates arrive out of index order across
-// tiles' halves, so a candidate is skipped only when its lower bound proves
-// h > h* (index below the best) or h > h* - 1 (index above it).
-template <int NS, int G>
-__device__ __forceinline__ void red_pass2(RowState& st, const float (&x)[4 * G][8],
-                                          const float (&c)[4 * G], float mn, const float (&gm)[G],
-                                          const float* __restrict__ cf, int g0, int col_base,
-                                          float na, float delta, float inv_n, int sr,
-                                          const ColExact* __restrict__ ci, int dn,
-                                          const StepParams* __restrict__ spp)
+// 32 lanes x 8 columns, waited for (the values of one domain in the exact
+// re-score below).
+__device__ __forceinline__ void tmem_ld8_wait(uint32_t taddr, float (&v)[8])
 {
-    // Compact code on purpose: this path is rare; the batch goes to a local
-    // copy, indexed in rolled loops, while the other warps keep working.
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]),
+                   "=f"(v[6]), "=f"(v[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]),
+                   "+f"(v[6]), "+f"(v[7])
+                 :
+                 : "memory");
+}
+
+// Exact re-scoring of the candidates of a batch of 4 G domains (maxima c)
+// whose filter is within 2 delta of the batch minimum mn and under the
+// range's threshold.  Entered by the whole warp (cand: this lane has a
+// candidate): for each domain that some lane still needs, the warp reads its
+// eight isometries back from TMEM (tb: the batch's first column), so no
+// value of the batch stays in registers after the filter.  cf/ci: the
+// tile's filter constants and exact column sums, indexed by the domain
+// within the tile.  Candidates arrive out of index order across tiles, so a
+// candidate is skipped only when its lower bound proves h > h* (index below
+// the best) or h > h* - 1 (index above it).
+template <int NS, int G>
+__device__ __forceinline__ void red_rescore(RowState& st, bool cand, const float (&c)[4 * G], float mn,
+                                         const float (&gm)[G], uint32_t tb,
+                                         const float* __restrict__ cf, int g0, int col_base,
+                                         float na, float delta, float inv_n, int sr,
+                                         const ColExact* __restrict__ ci, int dn,
+                                         const StepParams* __restrict__ spp)
+{
     const StepParams& sp = *spp;
     constexpr int cw = 1 + NS;
-    float te = fminf(st.thr, __fadd_ru(mn, 2.0f * delta));
-    unsigned gmask = 0;
-#pragma unroll
-    for (int g = 0; g < G; ++g) gmask |= (gm[g] <= te) ? (1u << g) : 0u;
-    if (!gmask) return;
-    float xl[4 * G * 8], cl[4 * G];
-#pragma unroll
-    for (int d = 0; d < 4 * G; ++d) {
-        cl[d] = c[d];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) xl[d * 8 + k] = x[d][k];
-    }
+    float te = cand ? fminf(st.thr, __fadd_ru(mn, 2.0f * delta)) : -__int_as_float(0x7f800000);
 #pragma unroll 1
-    for (; gmask; gmask &= gmask - 1) {
-        const int g = __ffs(gmask) - 1;
+    for (int g = 0; g < G; ++g) {
+        float gmg = gm[0];
+#pragma unroll
+        for (int j = 1; j < G; ++j)
+            if (g == j) gmg = gm[j];
+        if (!__any_sync(0xffffffffu, gmg <= te)) continue;
         const float* cg = cf + (size_t)(g0 + g) * cw * 4;
 #pragma unroll 1
         for (int e = 0; e < 4; ++e) {
             const int d = 4 * g + e;
+            float cmax = c[0];
+#pragma unroll
+            for (int j = 1; j < 4 * G; ++j)
+                if (d == j) cmax = c[j];
             float fm = __int_as_float(0x7f800000);
 #pragma unroll
-            for (int s = 0; s < NS; ++s) fm = fminf(fm, col_filter(cg, e, na, cl[d], sp, s));
-            if (!(fm <= te)) continue;
+            for (int s = 0; s < NS; ++s) fm = fminf(fm, col_filter(cg, e, na, cmax, sp, s));
+            const bool need = fm <= te;
+            if (!__any_sync(0xffffffffu, need)) continue;
+            float v[8];
+            __syncwarp();
+            tmem_ld8_wait(tb + (uint32_t)(8 * d), v);  // the whole warp reads the domain
+            if (need) {
             const int col = (g0 + g) * 4 + e + col_base;
-#pragma unroll 1
+#pragma unroll
             for (int k = 0; k < 8; ++k) {
-                const float xj = xl[d * 8 + k];
+                const float xj = v[k];
                 float fj = __int_as_float(0x7f800000), lo = fj;
 #pragma unroll
                 for (int s = 0; s < NS; ++s) {
@@ -268,6 +287,7 @@ __device__ __forceinline__ void red_pass2(RowState& st, const float (&x)[4 * G][
                 st = exact_col(st, xj, cg, e, col, (unsigned)k, na, delta, inv_n, sr,
                                ci + (g0 + g) * 4 + e, dn, spp, te);
                 te = fminf(te, st.thr);
+            }
             }
         }
     }
@@ -574,20 +594,19 @@ contract_tc_red_kernel(const __grid_constant__ RedParams P, const __grid_constan
                         float4 cc[kBatch / 4][1 + NS];
                         red_consts<NS, kBatch / 4>(cfs, g0, cc);
                         tmem_wait_batch(x, mx);
-                        if (bt == kDom / kBatch - 1) {
-                            // the tile is in registers: hand the slot back to the MMA
-                            tc_fence_before();
-                            __syncwarp();
-                            if (lane == 0) mbar_arrive(tempty(par));
-                        }
-                        if (valid) {
-                            float gm[kBatch / 4];
-                            const float mn = red_pass1<NS, kBatch / 4>(mx, cc, -r.a, sp, gm);
-                            if (mn <= st.thr)
-                                red_pass2<NS, kBatch / 4>(st, x, mx, mn, gm, cfs, g0, ct * kDom,
-                                                          -r.a, r.delta, inv_n, r.sr, cis, qdn, &sp);
-                        }
+                        float gm[kBatch / 4];
+                        const float mn = red_pass1<NS, kBatch / 4>(mx, cc, -r.a, sp, gm);
+                        const bool cand = valid && mn <= st.thr;
+                        if (__any_sync(0xffffffffu, cand))
+                            red_rescore<NS, kBatch / 4>(st, cand, mx, mn, gm,
+                                                        tb + (uint32_t)(8 * bt * kBatch), cfs, g0,
+                                                        ct * kDom, -r.a, r.delta, inv_n, r.sr, cis,
+                                                        qdn, &sp);
                     }
+                    // the tile's candidates are scored: hand the slot back to the MMA
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(tempty(par));
                     tphase ^= 1;
                     if (st.h < gpub) {
                         atomicMin(gb, st.h);
