@@ -551,8 +551,8 @@ def run_gpu(args):
                      "unit": "TFLOP/s", "frac": (achieved / peak_tf) if achieved else None,
                      "traffic": None if args.only_side else measured_traffic(),
                      "traffic_unit": "bytes per contraction launch (mean of the 3 steps)",
-                     "kernel": "contraction (contract_tc_kernel at 16x16, "
-                               "contract_tc_iso_kernel at 8x8 and 4x4)",
+                     "kernel": "contraction (the tuner's kernel per step: contract_tc_kernel "
+                               "at 16x16, contract_tc_red_kernel at 8x8 and 4x4)",
                      "algorithmic_flops_per_encode": tc["flops"] / max(args.steps, 1),
                      "timing": "library CUDA events around each contraction launch on the "
                                "launching stream, over a second pass of the same steps with "

@@ -335,19 +335,21 @@ const char* fic_strerror(int status);
 /* Contraction shape tuning                                            */
 /* ------------------------------------------------------------------ */
 /* The contraction of a quadtree step can run with several tile shapes that
- * give identical records: isometry-in-accumulator tiles (128 ranges x 64
- * pool domains x 8 isometries; 2x2 to 8x8 ranges with at most 3 S values)
- * or row tiles (128 (range, isometry) rows x 256 domains), each with a work
- * chunking tuned for a per-item refill cost of 1, 2 or 4 tiles, and for
- * isometry tiles 8 or 16 epilogue warps.  In mode 1
+ * give identical records: domain-side isometry tiles (128 ranges x 32 pool
+ * domains x 8 isometries, the maximum over the isometries taken by the
+ * tensor-memory load; 2x2 to 8x8 ranges with at most 3 S values),
+ * isometry-in-accumulator tiles (128 ranges x 64 domains x 8 isometries,
+ * same steps) or row tiles (128 (range, isometry) rows x 256 domains), each
+ * with a work chunking tuned for a per-item refill cost of 1, 2 or 4 tiles,
+ * and for isometry-in-accumulator tiles 8 or 16 epilogue warps.  In mode 1
  * (the default) the first step of each (engine, K = B*B padded, |S|, size
- * class = floor(log2(ranges x pool domains))) runs every candidate once on
+ * class = floor(log2(ranges x pool domains))) runs every candidate twice on
  * its own operands, timed with CUDA events, and keeps the fastest for that
  * class (one table per process, shared by the synchronous entry points and
  * the servers; a server never runs the candidates itself: a class without
  * an entry takes the nearest tuned class of the same (engine, K, |S|), else
- * the default).  Mode 0: the fixed default (isometry tiles
- * where they apply, 8 epilogue warps, refill 2); mode 2 + i: candidate i
+ * the default).  Mode 0: the fixed default (domain-side isometry tiles
+ * where they apply, refill 2); mode 2 + i: candidate i
  * for every step
  * (i taken modulo the step's candidate count).  The paper has no
  * counterpart; this is the GPU design's tile-shape choice. */
@@ -356,9 +358,10 @@ typedef struct {
     int32_t iso_tiles;                   /* 0: row tiles; 1: isometry tiles; 2: domain-side
                                             isometries, maximum by the TMEM load */
     int32_t refill;                      /* chunking refill cost, tiles     */
-    int32_t epi_warps;                   /* epilogue warps (isometry tiles:
-                                            8 with 16-column TMEM reads, or
-                                            16 with 8-column reads)        */
+    int32_t epi_warps;                   /* epilogue warps (isometry-in-
+                                            accumulator tiles: 8 with 16-column
+                                            TMEM reads, or 16 with 8-column
+                                            reads; domain-side tiles: 8)   */
     float ms;                            /* measured contraction time       */
     int32_t candidates;                  /* shapes measured                 */
 } fic_tune_entry;

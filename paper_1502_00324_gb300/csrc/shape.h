@@ -69,7 +69,9 @@ inline StepShape step_shape(const fic_params& p, int lvl, const TuneChoice& v)
     return h;
 }
 
-inline TuneChoice default_choice() { return TuneChoice{1, 2, 0}; }
+// Default (untuned) shape: the domain-side isometry kernel where it applies
+// (2x2 .. 8x8 steps with |S| <= 3), else the row kernel.
+inline TuneChoice default_choice() { return TuneChoice{2, 2, 0}; }
 
 inline int64_t rows_pad_for(const StepShape& h, int64_t R)
 {
