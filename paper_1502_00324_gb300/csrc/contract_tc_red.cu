@@ -240,6 +240,9 @@ __device__ __forceinline__ void red_rescore(RowState& st, bool cand, const float
     const StepParams& sp = *spp;
     constexpr int cw = 1 + NS;
     float te = cand ? fminf(st.thr, __fadd_ru(mn, 2.0f * delta)) : -__int_as_float(0x7f800000);
+    // h*/n and (h* - 1)/n rounded up, converted again only when the best changes
+    long long hc = kNoCandidate;
+    float hb_eq = 0.0f, hb_below = 0.0f;
 #pragma unroll 1
     for (int g = 0; g < G; ++g) {
         float gmg = gm[0];
@@ -280,17 +283,39 @@ __device__ __forceinline__ void red_rescore(RowState& st, bool cand, const float
                 }
                 if (!(fj <= te)) continue;
                 if (st.h != kNoCandidate) {
-                    const long long bound =
-                        pack_idx((unsigned)col, (unsigned)k, 0) > st.idx ? st.h - 1 : st.h;
-                    if (lo > __ll2float_ru(bound) * inv_n) continue;
+                    if (st.h != hc) {
+                        hc = st.h;
+                        hb_eq = __ll2float_ru(hc) * inv_n;
+                        hb_below = __ll2float_ru(hc - 1) * inv_n;
+                    }
+                    if (lo > (pack_idx((unsigned)col, (unsigned)k, 0) > st.idx ? hb_below : hb_eq))
+                        continue;
                 }
-                st = exact_col(st, xj, cg, e, col, (unsigned)k, na, delta, inv_n, sr,
-                               ci + (g0 + g) * 4 + e, dn, spp, te);
+                st = exact_col_inl(st, xj, cg, e, col, (unsigned)k, na, delta, inv_n, sr,
+                                   ci + (g0 + g) * 4 + e, dn, spp, te);
                 te = fminf(te, st.thr);
             }
             }
         }
     }
+}
+
+// Out-of-line entry of the re-score, which is rare: scalar arguments and the
+// row state by value, so that the kernel's live registers are saved once per
+// entry and nothing of the caller has to live in memory.
+template <int NS>
+__device__ __noinline__ RowState red_rescore_call(RowState st, bool cand, float c0, float c1, float c2,
+                                                  float c3, float c4, float c5, float c6, float c7,
+                                                  float mn, float gm0, float gm1, uint32_t tb,
+                                                  const float* __restrict__ cf, int g0, int col_base,
+                                                  float na, float delta, float inv_n, int sr,
+                                                  const ColExact* __restrict__ ci, int dn,
+                                                  const StepParams* __restrict__ spp)
+{
+    const float c[8] = {c0, c1, c2, c3, c4, c5, c6, c7};
+    const float gm[2] = {gm0, gm1};
+    red_rescore<NS, 2>(st, cand, c, mn, gm, tb, cf, g0, col_base, na, delta, inv_n, sr, ci, dn, spp);
+    return st;
 }
 
 template <int B>
@@ -597,11 +622,13 @@ contract_tc_red_kernel(const __grid_constant__ RedParams P, const __grid_constan
                         float gm[kBatch / 4];
                         const float mn = red_pass1<NS, kBatch / 4>(mx, cc, -r.a, sp, gm);
                         const bool cand = valid && mn <= st.thr;
+                        static_assert(kBatch == 8, "the re-score entry takes 8 maxima");
                         if (__any_sync(0xffffffffu, cand))
-                            red_rescore<NS, kBatch / 4>(st, cand, mx, mn, gm,
-                                                        tb + (uint32_t)(8 * bt * kBatch), cfs, g0,
-                                                        ct * kDom, -r.a, r.delta, inv_n, r.sr, cis,
-                                                        qdn, &sp);
+                            st = red_rescore_call<NS>(st, cand, mx[0], mx[1], mx[2], mx[3], mx[4],
+                                                      mx[5], mx[6], mx[7], mn, gm[0], gm[1],
+                                                      tb + (uint32_t)(8 * bt * kBatch), cfs, g0,
+                                                      ct * kDom, -r.a, r.delta, inv_n, r.sr, cis,
+                                                      qdn, &sp);
                     }
                     // the tile's candidates are scored: hand the slot back to the MMA
                     tc_fence_before();

@@ -71,12 +71,12 @@ __device__ __forceinline__ float col_filter(const float* __restrict__ cg, int e,
 }
 
 // Exact re-scoring of one column for the S values whose filter passes te.
-// Out of line: it runs rarely, and a call keeps the caller's register
-// arrays statically indexed.
-static __device__ __noinline__ RowState exact_col(RowState st, float x, const float* __restrict__ cg,
-                                           int e, int col, unsigned iso, float na, float delta,
-                                           float inv_n, int sr, const ColExact* __restrict__ cep,
-                                           int dn, const StepParams* __restrict__ spp, float te)
+static __device__ __forceinline__ RowState exact_col_inl(RowState st, float x,
+                                                        const float* __restrict__ cg, int e, int col,
+                                                        unsigned iso, float na, float delta,
+                                                        float inv_n, int sr,
+                                                        const ColExact* __restrict__ cep, int dn,
+                                                        const StepParams* __restrict__ spp, float te)
 {
     const StepParams& sp = *spp;
     if (col >= dn) return st;
@@ -95,6 +95,16 @@ static __device__ __noinline__ RowState exact_col(RowState st, float x, const fl
         }
     }
     return st;
+}
+
+// The same out of line: it runs rarely, and a call keeps the caller's
+// register arrays statically indexed.
+static __device__ __noinline__ RowState exact_col(RowState st, float x, const float* __restrict__ cg,
+                                           int e, int col, unsigned iso, float na, float delta,
+                                           float inv_n, int sr, const ColExact* __restrict__ cep,
+                                           int dn, const StepParams* __restrict__ spp, float te)
+{
+    return exact_col_inl(st, x, cg, e, col, iso, na, delta, inv_n, sr, cep, dn, spp, te);
 }
 
 // Process NG groups of 4 consecutive columns of one row: group g holds
