@@ -74,3 +74,27 @@ def test_tuned_classes_are_recorded(pkg):
     b = pkg.fic_encode_ex(img, 160, 16, 4, 1, -1.0, ss, 8.0)
     assert len(pkg.fic_tune_read()) == n
     np.testing.assert_array_equal(a.codes, b.codes)
+
+
+@pytest.mark.parametrize("kind", ["black", "binary_noise", "checker"])
+def test_forced_shapes_on_extreme_images(pkg, kind):
+    """The domain-side kernel (mode 7) and the isometry-in-accumulator kernel
+    (mode 2) on the extremes of the centred operands, with 2x2 ranges: the
+    all-black image gives the largest partial sums and all-equal filter values
+    (every tie broken by the index), noise and checkerboards mix signs and
+    isometries that map a block onto itself."""
+    N = 64
+    rng = np.random.default_rng(11)
+    if kind == "black":
+        img = np.zeros((N, N), np.uint8)
+    elif kind == "binary_noise":
+        img = (rng.integers(0, 2, (N, N)) * 255).astype(np.uint8)
+    else:
+        img = (((np.indices((N, N)).sum(0)) % 2) * 255).astype(np.uint8)
+    ss = [PAPER_S[s] for s in (16, 8, 4, 2)]
+    want, _ = oracle.encode(img, 16, 2, 1, -1.0, ss, 4.0)
+    for mode in (2, 7):
+        pkg.fic_tune_mode(mode)
+        enc = pkg.fic_encode_ex(img, N, 16, 2, 1, -1.0, ss, 4.0)
+        assert_same_codes(enc.codes, want, 16, f"{kind} mode {mode}")
+    pkg.fic_tune_mode(1)
