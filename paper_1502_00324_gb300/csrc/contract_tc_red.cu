@@ -114,6 +114,39 @@ __host__ __device__ constexpr int iso_src_pixel(int B, int k, int t)
     return i * B + j;
 }
 
+// Build-time checks of the map against the definitions above: each T_k is
+// a permutation of the B x B pixels, rot^4 and mirror^2 are the identity,
+// and a few entries written out from rot(x)[i][j] = x[B-1-j][i] and
+// mirror(x)[i][j] = x[i][B-1-j].
+__host__ __device__ constexpr bool iso_map_is_permutation(int B, int k)
+{
+    for (int s = 0; s < B * B; ++s) {
+        int hits = 0;
+        for (int t = 0; t < B * B; ++t) hits += iso_src_pixel(B, k, t) == s ? 1 : 0;
+        if (hits != 1) return false;
+    }
+    return true;
+}
+__host__ __device__ constexpr bool iso_maps_ok(int B)
+{
+    for (int k = 0; k < 8; ++k)
+        if (!iso_map_is_permutation(B, k)) return false;
+    for (int t = 0; t < B * B; ++t) {
+        // four quarter turns, and rot^2 applied twice, give back every pixel
+        int u = t;
+        for (int r = 0; r < 4; ++r) u = iso_src_pixel(B, 1, u);
+        if (u != t || iso_src_pixel(B, 2, iso_src_pixel(B, 2, t)) != t) return false;
+        // the mirror is an involution
+        if (iso_src_pixel(B, 4, iso_src_pixel(B, 4, t)) != t) return false;
+    }
+    return true;
+}
+static_assert(iso_maps_ok(2) && iso_maps_ok(4) && iso_maps_ok(8), "isometry maps");
+static_assert(iso_src_pixel(4, 1, 1) == 8, "rot(x)[0][1] = x[2][0]");
+static_assert(iso_src_pixel(4, 4, 0) == 3, "mirror(x)[0][0] = x[0][3]");
+static_assert(iso_src_pixel(4, 5, 1) == 4, "mirror o rot (x)[0][1] = x[1][0]: the transpose");
+static_assert(iso_src_pixel(8, 7, 0) == 63, "mirror o rot^3 (x)[0][0] = x[7][7]");
+
 // Word w (pixels 2w, 2w + 1) of T_k(x), x given as K/2 words of two halves
 // (pixels past B x B are the zero padding of K).
 template <int B, int k, int w, int NW>
@@ -678,7 +711,9 @@ size_t red_layout(int cw, int* nraw_out, int* nstage_out, int* ncf_out)
 {
     using Lay = RedLayout<B>;
     const size_t cf_tile = (size_t)kDom * cw * 4 + (size_t)kDom * sizeof(ColExact);
-    const int ncf = 16, nraw = Lay::K == 64 ? 8 : 16;  // ncf even: entry c serves tile parity c % 2
+    constexpr int ncf = 16;  // even: constants entry c serves the tiles of parity c % 2
+    static_assert(ncf % 2 == 0, "constants ring of whole tile pairs");
+    const int nraw = Lay::K == 64 ? 8 : 16;
     const size_t fixed = Lay::kAbytes + (size_t)nraw * Lay::kRawBytes + (size_t)ncf * cf_tile + 1024;
     int ns = (int)((kSmemBudget - fixed) / Lay::kStageBytes);
     if (ns > 8) ns = 8;
